@@ -1,0 +1,320 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle (``oracle/``) against something other than
+itself: closed-form spectra, a brute-force dense eigensolve, the optimal
+line-search step of Lemma 3 (Sec. 4), the special cases the paper names
+(TRLan for M = I and l = 0, Sec. 5.2; LOPCG for one inner step, Sec. 5.1;
+the Krylov space for a single restart vector, Sec. 4.2), the matvec
+accounting behind Tables 2-5, and invariants (B-orthonormality,
+T = U^T A U, monotone Ritz values).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+import scipy.sparse as sp
+
+from oracle import dense
+from oracle import trplk as O
+from paper_1711_10128_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def lap2d_eigs(N, count):
+    h = math.pi / (2 * (N + 1))
+    ev = sorted(4 * math.sin(i * h) ** 2 + 4 * math.sin(j * h) ** 2
+                for i in range(1, N + 1) for j in range(1, N + 1))
+    return np.array(ev[:count])
+
+
+def lap3d_eigs(N, count):
+    s = 4 * np.sin(np.arange(1, N + 1) * np.pi / (2 * (N + 1))) ** 2
+    return np.sort((s[:, None, None] + s[None, :, None] + s[None, None, :]).ravel())[:count]
+
+
+def fem_eigs(N, count):
+    h = 1.0 / N
+    t = (2 * np.arange(1, N + 1) - 1) * np.pi / (2 * N)
+    mu = (6 / h ** 2) * (1 - np.cos(t)) / (2 + np.cos(t))
+    return np.sort((mu[:, None, None] + mu[None, :, None] + mu[None, None, :]).ravel())[:count]
+
+
+# ---------------------------------------------------------------- dense pieces
+@pytest.mark.parametrize("n", [1, 2, 7, 31])
+def test_jacobi_eigh_tridiagonal_closed_form(n):
+    T = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    w, V = dense.jacobi_eigh(T)
+    ref = 2 - 2 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1))
+    assert np.allclose(w, np.sort(ref), atol=1e-13)
+    assert np.allclose(T @ V, V * w, atol=1e-12)
+    assert np.allclose(V.T @ V, np.eye(n), atol=1e-13)
+
+
+def test_jacobi_eigh_matches_lapack_random():
+    rng = np.random.default_rng(5)
+    for n in (3, 16, 50):
+        M = rng.standard_normal((n, n))
+        M = M + M.T
+        w, V = dense.jacobi_eigh(M)
+        assert np.allclose(w, np.linalg.eigvalsh(M), atol=1e-12 * np.abs(w).max())
+        assert np.allclose(M @ V, V * w, atol=1e-12 * np.abs(w).max())
+
+
+def test_rayleigh_ritz_against_dense_jacobi_and_sign_rule():
+    rng = np.random.default_rng(7)
+    M = rng.standard_normal((12, 12))
+    M = M + M.T
+    theta, Y = O.rayleigh_ritz(np.triu(M))     # only the upper triangle is read
+    w, V = dense.jacobi_eigh(M)
+    assert np.allclose(theta, w, atol=1e-12)
+    for c in range(12):
+        i = np.argmax(np.abs(Y[:, c]))
+        assert Y[i, c] > 0
+        assert abs(abs(V[:, c] @ Y[:, c]) - 1) < 1e-10
+
+
+def test_two_vector_rayleigh_ritz_matches_lemma3_optimal_step():
+    """Lemma 3 (Sec. 4): min over span{x, d} of the Rayleigh quotient of
+    (A, B) is reached at x + alpha* d, alpha* the smaller positive (or the
+    unique) root of a alpha^2 + b alpha + c = 0."""
+    A, B = W.fem_q1_pencil(4)
+    A, B = A.to_scipy().toarray(), B.to_scipy().toarray()
+    rng = np.random.default_rng(3)
+    v1 = sl.eigh(A, B)[1][:, 0]
+    x = v1 + 0.05 * rng.standard_normal(v1.size)
+    x /= math.sqrt(x @ B @ x)
+    rho = x @ A @ x
+    grad = A @ x - rho * B @ x
+    d = -grad + 0.1 * rng.standard_normal(x.size)        # a descent direction
+    assert d @ grad < 0
+    a = (d @ A @ d) * (d @ B @ x) - (d @ B @ d) * (d @ A @ x)
+    b = (d @ A @ d) * (x @ B @ x) - (d @ B @ d) * (x @ A @ x)
+    c = (d @ A @ x) * (x @ B @ x) - (d @ B @ x) * (x @ A @ x)
+    roots = np.roots([a, b, c]) if abs(a) > 0 else np.array([-c / b])
+    roots = np.real(roots[np.isreal(roots)])
+    alpha = roots[roots > 0].min()
+    y = x + alpha * d
+    rq_opt = (y @ A @ y) / (y @ B @ y)
+    # the oracle's pieces: B-orthonormalise [x, d], project, Rayleigh-Ritz
+    Bfun = lambda v: B @ v
+    Q, BQ, _ = O.b_orthonormalise(np.stack([x, d], axis=1), Bfun)
+    T = Q.T @ A @ Q
+    theta, _ = O.rayleigh_ritz(T)
+    assert abs(theta[0] - rq_opt) <= 1e-12 * abs(rq_opt)
+
+
+def test_cgs2_b_orthogonality_and_norm():
+    A, B = W.fem_q1_pencil(5)
+    Bs = B.to_scipy()
+    rng = np.random.default_rng(11)
+    n = Bs.shape[0]
+    Bfun = lambda v: Bs @ v
+    U, BU, _ = O.b_orthonormalise(rng.standard_normal((n, 9)), Bfun)
+    assert np.allclose(U.T @ (Bs @ U), np.eye(9), atol=1e-13)
+    w = rng.standard_normal(n)
+    wo, Bw, beta, beta0, h = O.cgs2(w, U, BU, Bfun)
+    assert np.abs(U.T @ (Bs @ wo)).max() <= 1e-13 * beta
+    assert abs(beta - math.sqrt(wo @ (Bs @ wo))) <= 1e-13 * beta
+    assert abs(beta0 - math.sqrt(w @ (Bs @ w))) <= 1e-12 * beta0
+    # w = U h + wo exactly (up to rounding)
+    assert np.allclose(U @ h + wo, w, atol=1e-12 * np.abs(w).max())
+
+
+# ---------------------------------------------------------------- whole solves
+def kato_temple_ok(theta, lam, rnorm, gap):
+    return abs(theta - lam) <= rnorm ** 2 / gap + 1e-14 * abs(lam) + rnorm * 1e-8
+
+
+@pytest.mark.parametrize("N,p,q,k,l", [(30, 5, 20, 8, 5), (24, 3, 12, 4, 1)])
+def test_solve_2d_laplacian_closed_form(N, p, q, k, l):
+    A = W.laplacian_2d(N)
+    As = A.to_scipy()
+    X0 = W.start_block(A.n, k, 0)
+    r = O.solve(As, None, p, q, k, l, 1e-10, X0, "jacobi")
+    assert r["status"] == O.OK
+    lam = lap2d_eigs(N, p + 1)
+    gap = lam[p] - lam[p - 1] if lam[p] > lam[p - 1] else lam[p] - lam[0]
+    rabs = r["resid"] * r["normA"]
+    for i in range(p):
+        assert abs(r["evals"][i] - lam[i]) <= 1e-9 * lam[i]
+        # Krylov-Weinstein: |theta - lambda| <= ||r|| for B = I
+        assert np.min(np.abs(lap2d_eigs(N, 2 * p + 2) - r["evals"][i])) <= rabs[i] + 1e-15
+    assert np.all(r["resid"] <= 1e-10)
+    X = r["evecs"]
+    assert np.allclose(X.T @ X, np.eye(p), atol=1e-12)
+    # matvec accounting of Tables 2-5: p_hat + (q - p_hat) * cycles
+    assert r["mv_A"] == k + (q - k) * r["cycles"]
+
+
+def test_full_size_2d_laplacian_100():
+    """The 100 x 100 Laplacian with p = 5, q = 20, p_hat = 8, +K = 5, tol 1e-8."""
+    N, p, q, k, l = 100, 5, 20, 8, 5
+    A = W.laplacian_2d(N)
+    r = O.solve(A.to_scipy(), None, p, q, k, l, 1e-8, W.start_block(A.n, k, 0), "jacobi")
+    assert r["status"] == O.OK
+    lam = lap2d_eigs(N, p)
+    # error bounded by ||r||^2 / gap (Kato-Temple) with ||r|| <= 1e-8 * ||A||_1
+    assert np.all(np.abs(r["evals"] - lam) <= (8e-8) ** 2 / 1e-3 + 1e-13)
+    assert np.all(r["resid"] <= 1e-8)
+    assert r["mv_A"] == k + (q - k) * r["cycles"]
+
+
+def test_solve_3d_isotropic_closed_form():
+    N = 12
+    A = W.diffusion_3d(N)
+    p, q, k, l = 4, 16, 6, 1
+    r = O.solve(A.to_scipy(), None, p, q, k, l, 1e-10, W.start_block(A.n, k, 1), "jacobi")
+    assert r["status"] == O.OK
+    lam = lap3d_eigs(N, p)
+    assert np.all(np.abs(r["evals"] - lam) <= 1e-9 * lam)
+
+
+def test_solve_generalized_fem_pencil_closed_form_and_brute_force():
+    N = 6
+    A, B = W.fem_q1_pencil(N)
+    As, Bs = A.to_scipy(), B.to_scipy()
+    p, q, k, l = 5, 18, 8, 1
+    r = O.solve(As, Bs, p, q, k, l, 1e-10, W.start_block(A.n, k, 2), "jacobi")
+    assert r["status"] == O.OK
+    lam = fem_eigs(N, p)
+    brute = sl.eigh(As.toarray(), Bs.toarray(), eigvals_only=True)[:p]
+    assert np.allclose(lam, brute, rtol=1e-11)
+    assert np.all(np.abs(r["evals"] - lam) <= 1e-9 * lam)
+    X = r["evecs"]
+    assert np.allclose(X.T @ (Bs @ X), np.eye(p), atol=1e-11)
+    assert r["mv_A"] == k + (q - k) * r["cycles"]
+    assert r["mv_B"] == r["mv_A"]
+
+
+def test_solve_variable_coefficient_brute_force():
+    N = 10
+    A = W.diffusion_3d(N, W.lognormal_field(N, 1.0, 4))
+    As = A.to_scipy()
+    p, q, k, l = 6, 20, 8, 2
+    r = O.solve(As, None, p, q, k, l, 1e-10, W.start_block(A.n, k, 3), "jacobi")
+    assert r["status"] == O.OK
+    brute = np.linalg.eigvalsh(As.toarray())[:p]
+    assert np.all(np.abs(r["evals"] - brute) <= 1e-9 * brute)
+
+
+def test_invariants_T_equals_UtAU_and_b_orthonormal_basis():
+    N = 5
+    A, B = W.fem_q1_pencil(N, np.random.default_rng(0).uniform(1, 10, (N, N, N)))
+    As, Bs = A.to_scipy(), B.to_scipy()
+    r = O.solve(As, Bs, 3, 14, 5, 2, 1e-10, W.start_block(A.n, 5, 9), "jacobi",
+                max_cycles=4, record=True)
+    for tr in r["trace"]:
+        U = tr["U"]
+        assert np.allclose(U.T @ (Bs @ U), np.eye(U.shape[1]), atol=1e-12)
+        TA = U.T @ (As @ U)
+        assert np.allclose(tr["T"], TA, atol=1e-11 * np.abs(TA).max())
+        assert np.allclose(tr["AU"], As @ U, atol=1e-12 * np.abs(tr["AU"]).max())
+        assert np.allclose(tr["BU"], Bs @ U, atol=1e-12 * np.abs(tr["BU"]).max())
+    # after restart T(1:p_hat, 1:p_hat) = diag(theta) (Sec. 3)
+    T1 = r["trace"][1]["T"]
+    th0 = r["trace"][0]["theta"][:5]
+    assert np.allclose(T1[:5, :5], np.diag(th0), atol=1e-12 * np.abs(th0).max())
+
+
+def test_ritz_values_never_increase():
+    """The restart space contains the previous p_hat Ritz vectors, so by the
+    Courant-Fischer minimax property every kept Ritz value can only decrease."""
+    A = W.diffusion_3d(9, W.lognormal_field(9, 1.0, 6))
+    r = O.solve(A.to_scipy(), None, 4, 14, 6, 1, 1e-12, W.start_block(A.n, 6, 4), "jacobi",
+                max_cycles=30)
+    th = np.array([h["theta"] for h in r["history"]])
+    assert np.all(np.diff(th, axis=0) <= 1e-12 * np.abs(th).max())
+
+
+def test_trlan_special_case_tridiagonal_g_block():
+    """M = I and l = 0: TRPL+K reduces to thick-restart Lanczos (Sec. 5.2), so the
+    G-G block of T obeys the Lanczos three-term relation (is tridiagonal)."""
+    A = W.diffusion_3d(8, W.lognormal_field(8, 1.0, 2))
+    k = 4
+    r = O.solve(A.to_scipy(), None, 2, 14, k, 0, 1e-12, W.start_block(A.n, k, 5), "none",
+                max_cycles=3, record=True)
+    for tr in r["trace"]:
+        G = tr["T"][k:, k:]
+        scale = np.abs(G).max()
+        off = np.abs(np.triu(G, 2)).max()
+        assert off <= 1e-10 * scale
+        assert np.abs(np.diag(G, 1)).min() > 1e-6 * scale
+
+
+def test_single_vector_basis_is_preconditioned_krylov_space():
+    """p_hat = 1: span{x, G} = K_{m+1}(M (A - rho B), x) (Sec. 4.2)."""
+    A = W.diffusion_3d(7, W.lognormal_field(7, 1.0, 8))
+    As = A.to_scipy()
+    dinv = 1.0 / As.diagonal()
+    q = 7
+    r = O.solve(As, None, 1, q, 1, 1, 1e-14, W.start_block(A.n, 1, 6), "jacobi",
+                max_cycles=1, record=True)
+    tr = r["trace"][0]
+    U, rho = tr["U"], tr["rho"]
+    x = U[:, 0]
+    K = [x]
+    for _ in range(q - 1):
+        v = dinv * (As @ K[-1] - rho * K[-1])
+        K.append(v / np.linalg.norm(v))
+    Qk, _ = np.linalg.qr(np.stack(K, axis=1))
+    s = np.linalg.svd(Qk.T @ U, compute_uv=False)
+    assert s.min() > 1 - 1e-8
+
+
+def test_lopcg_special_case():
+    """p_hat = 1, one inner step and l = 1: the space is span{x_i, M r_i, x_(i-1)},
+    LOPCG's (Sec. 5.1; eq. (subspace_lobpcg) with p = 1).  An independent loop
+    using Gram matrices of the raw vectors reproduces the Ritz values."""
+    A = W.diffusion_3d(8, W.lognormal_field(8, 0.5, 12))
+    As = A.to_scipy()
+    dinv = 1.0 / As.diagonal()
+    x0 = W.start_block(A.n, 1, 7)[:, 0]
+    r = O.solve(As, None, 1, 3, 1, 1, 1e-30, x0[:, None], "jacobi", max_cycles=12)
+    ours = [h["theta"][0] for h in r["history"]]
+
+    def rr(V):
+        G = V.T @ V
+        H = V.T @ (As @ V)
+        w, Y = sl.eigh(H, G)
+        y = V @ Y[:, 0]
+        return w[0], y / np.linalg.norm(y)
+
+    x = x0 / np.linalg.norm(x0)
+    rho = x @ (As @ x)
+    # first cycle: no previous vector yet, two inner steps (m = q - p_hat = 2)
+    g1 = dinv * (As @ x - rho * x)
+    g2 = dinv * (As @ g1 - rho * g1)
+    th, xn = rr(np.stack([x, g1, g2], axis=1))
+    ref = [th]
+    xprev, x = x, xn
+    for _ in range(11):
+        rho = x @ (As @ x)
+        g1 = dinv * (As @ x - rho * x)
+        th, xn = rr(np.stack([x, g1, xprev], axis=1))
+        ref.append(th)
+        xprev, x = x, xn
+    ours, ref = np.array(ours), np.array(ref)
+    assert np.allclose(ours, ref, rtol=1e-9, atol=1e-12)
+
+
+def test_paper_matvec_counts_follow_restart_accounting():
+    """Every TRPL+K MV count printed in Tables 2-5 equals p_hat + (q - p_hat) c
+    for an integer cycle count c, with p_hat = 8, q = 18 (Sec. 5 setup): the
+    accounting the oracle's counter follows."""
+    rows = [line.split() for line in open(os.path.join(GOLDEN, "paper_mv_counts.txt"))
+            if line.strip() and not line.startswith("#")]
+    assert len(rows) == 22
+    for table, name, p, mv in rows:
+        assert (int(mv) - 8) % 10 == 0, (table, name, mv)
+
+
+def test_closed_form_values_c1():
+    """The 2D formula evaluated for the 100 x 100 grid (checks its transcription)."""
+    lam = lap2d_eigs(100, 6)
+    assert abs(lam[0] - 1.934870832047740e-3) < 1e-17
+    assert abs(lam[1] - lam[2]) < 1e-17 and abs(lam[3] - 7.737611465622606e-3) < 1e-17
+    brute = np.linalg.eigvalsh(W.laplacian_2d(12).to_scipy().toarray())[:6]
+    assert np.allclose(brute, lap2d_eigs(12, 6), rtol=1e-13)
