@@ -1,0 +1,227 @@
+/*
+ * trplk.h -- C ABI of libtrplk, a GB300 (sm_103a) implementation of the hot
+ * path of TRPL+K, the thick-restart preconditioned Lanczos method with +K
+ * (locally optimal) restarting of Wu, Xue and Stathopoulos (arXiv 1711.10128).
+ *
+ * The library finds the p smallest eigenpairs of a sparse symmetric pencil
+ * A v = lambda B v with B symmetric positive definite (Sec. 1, eq. (1)), with
+ * B-orthonormal eigenvectors.  Everything runs on one GPU in hand-written CUDA
+ * kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Sparse matrices are CSR with int64 row pointers (n + 1 entries,
+ *    rowptr[0] = 0), int32 column indices sorted within each row, and values
+ *    of the dtype named by the matrix (TRPLK_F64 = double, TRPLK_F32 = float).
+ *    A and B must be symmetric; the library does not check symmetry.
+ *  - Dense blocks of n-vectors are column-major with a leading dimension
+ *    `ld` >= n.  Inside the library ld is n rounded up to a multiple of 256 and
+ *    rows n..ld-1 are kept at zero; the step-level entry points below take the
+ *    caller's ld and require ld % 256 == 0 and the padding rows to be zero.
+ *  - Ownership: the caller owns every buffer it passes and every output
+ *    buffer; the library never frees caller memory.  Device pointers are used
+ *    in place and must stay valid for the duration of the call.  The library
+ *    owns its workspace until trplk_destroy.
+ *  - Every call is synchronous with respect to the host: it returns after its
+ *    GPU work on the handle's stream has finished (or failed).  One handle
+ *    must not be used by two threads at once.
+ *  - Errors: every entry point returns a trplk_status; on anything but
+ *    TRPLK_OK (and TRPLK_NOT_CONVERGED, whose outputs are still filled) the
+ *    outputs are unspecified and trplk_last_error() says why.  Invalid
+ *    arguments are detected on the host before any GPU work (TRPLK_EINVAL).
+ */
+#ifndef TRPLK_H_
+#define TRPLK_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TRPLK_ABI_VERSION 1
+
+typedef enum {
+  TRPLK_OK = 0,
+  TRPLK_EINVAL = 1,         /* bad argument (checked on the host)            */
+  TRPLK_ENOMEM = 2,         /* device allocation failed                      */
+  TRPLK_ECUDA = 3,          /* a CUDA call or kernel failed                  */
+  TRPLK_NOT_CONVERGED = 4,  /* max_cycles reached; outputs hold the best pairs */
+  TRPLK_BREAKDOWN = 5,      /* the Krylov space became invariant; no progress */
+  TRPLK_NOT_SPD_B = 6,      /* x^T B x <= 0 was observed                     */
+  TRPLK_NAN = 7,            /* a NaN or Inf reached a reduction              */
+  TRPLK_ETIMEOUT = 8        /* a bounded device-side wait ran out            */
+} trplk_status;
+
+enum { TRPLK_F64 = 0, TRPLK_F32 = 1 };
+enum { TRPLK_SMALLEST = 0 };
+enum {
+  TRPLK_PRECOND_NONE = 0,    /* M = I                                         */
+  TRPLK_PRECOND_JACOBI = 1,  /* M = diag(A)^-1                                */
+  TRPLK_PRECOND_FSAI = 2     /* M = G^T G from a caller-supplied factor G    */
+};
+enum {
+  TRPLK_PRECISION_FP64 = 0,  /* FP64 storage and arithmetic throughout        */
+  TRPLK_PRECISION_MIXED = 1  /* FP32 storage/SpMV, FP64-class coefficients,
+                                then FP64 refinement to tol                   */
+};
+
+typedef struct trplk_handle trplk_handle;
+
+/* A sparse symmetric matrix in CSR form.  `val` holds nnz values of `dtype`.
+ * on_device = 1: all three arrays are device pointers; 0: host pointers. */
+typedef struct {
+  int64_t n, nnz;
+  const int64_t* rowptr;
+  const int32_t* col;
+  const void* val;
+  int dtype;
+  int on_device;
+} trplk_csr;
+
+/* Solver parameters (Algorithm 1's inputs, Sec. 3, with the paper's names):
+ *  p          number of wanted (smallest) eigenpairs, 1 <= p <= k
+ *  q          maximum basis size (the paper's q = maxBasisSize), q <= 64
+ *  k          thick-restart size p_hat >= p (minRestartSize, Sec. 5), k <= 32
+ *  l          maximum number of +K (previous Ritz) vectors, 0 <= l,
+ *             q >= k + max(l, 1) + 1
+ *  tol        residual tolerance: ||A x - theta B x||_2 <= tol ||A||_1 ||x||_2
+ *  max_cycles maximum number of restart cycles (the paper's maxIter)
+ *  seed       SplitMix64 seed of the start block when X0 is NULL
+ *  which      TRPLK_SMALLEST (the only supported value)
+ *  precond    TRPLK_PRECOND_*
+ *  precision  TRPLK_PRECISION_*
+ *  outputs_on_device  1: evals/evecs/resid are device pointers; 0: host
+ *  fsai_*     the sparse lower-triangular factor G (CSR, F64 values, same
+ *             on_device as A) when precond = TRPLK_PRECOND_FSAI; M = G^T G
+ *  mixed_tol  FP32-phase tolerance of the mixed path (0 = 1e-6)          */
+typedef struct {
+  int p, q, k, l;
+  double tol;
+  int max_cycles;
+  uint64_t seed;
+  int which;
+  int precond;
+  int precision;
+  int outputs_on_device;
+  const trplk_csr* fsai_G;
+  double mixed_tol;
+} trplk_params;
+
+/* Counters and timings of one solve. */
+typedef struct {
+  int cycles;             /* restart cycles of the main phase                 */
+  int refine_cycles;      /* FP64 refinement cycles (mixed path)              */
+  int64_t mv_A, mv_B;     /* matvecs with A and B (B = I counts none)         */
+  int64_t prec_apply;     /* preconditioner applications                     */
+  int64_t mv_check;       /* matvecs of the final FP64 residual check         */
+  double seconds;         /* wall time of the call                            */
+  int nconv;              /* pairs meeting tol in the final check             */
+  double normA;           /* ||A||_1                                          */
+  double max_resid;       /* largest final relative residual                  */
+} trplk_info;
+
+/* Create a handle bound to CUDA device `device`.  cuda_stream: a
+ * cudaStream_t to run on, or NULL for a stream the library creates and owns.
+ * Returns TRPLK_EINVAL for a bad device, TRPLK_ECUDA if CUDA fails. */
+trplk_status trplk_create(trplk_handle** h, int device, void* cuda_stream);
+
+/* Destroy a handle and free its workspace.  NULL is accepted. */
+trplk_status trplk_destroy(trplk_handle* h);
+
+/* Text of the last error on this handle ("" if none).  Owned by the handle. */
+const char* trplk_last_error(const trplk_handle* h);
+
+/* ABI version of the loaded library (TRPLK_ABI_VERSION). */
+int trplk_abi_version(void);
+
+/* Solve A v = lambda B v for the p smallest eigenpairs by TRPL+K
+ * (Algorithm 1, Sec. 3; generalized pencil as sketched at the end of Sec. 3
+ * and in Algorithm 2, Sec. 4).
+ *  A, B     CSR (B == NULL: B = I); F64 values; same n.
+ *  X0       n x k column-major (ld = n) start block in host or device memory
+ *           (unified addressing tells them apart), or NULL to draw it with
+ *           SplitMix64 from params->seed
+ *  evals    [p] ascending Ritz values
+ *  evecs    n x p column-major (ld = n), B-orthonormal Ritz vectors
+ *  resid    [p] final FP64 relative residuals ||A x - theta B x|| / (||A||_1 ||x||)
+ *  info     counters (may be NULL)
+ * Returns TRPLK_OK when every pair meets tol, TRPLK_NOT_CONVERGED (outputs
+ * filled with the best pairs) after max_cycles, or an error code. */
+trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B,
+                         const trplk_params* params, const double* X0, double* evals,
+                         double* evecs, double* resid, trplk_info* info);
+
+/* ------------------------------------------------------------------------
+ * Step-level entry points: the kernels of the solver, one row of its hot
+ * path each, for parity tests and for callers that drive their own loop.
+ * All pointers are device pointers; `dtype` selects F64 or F32 storage of
+ * every dense array of the call (coefficients, T, theta, Y, norms are always
+ * double).  ld % 256 == 0, padding rows zero.
+ * ---------------------------------------------------------------------- */
+
+/* y = A x (the matvec of eq. (UpdateT)).  A on device, val of `A->dtype`;
+ * x, y of that dtype, length n.  y must not alias x. */
+trplk_status trplk_spmv(trplk_handle* h, const trplk_csr* A, const void* x, void* y);
+
+/* The fused T-column / preconditioner / first-projection pass of one inner
+ * step (eq. (UpdateT) and the Lanczos step after it):
+ *   tcol[0:w] = U[:, 0:w]^T z,  v = dinv .* (z - rho * bg),  h1[0:w] = BU[:, 0:w]^T v
+ * U, BU: n x w (ld); BU may equal U (B = I).  dinv, z, bg, v: vectors (ld);
+ * dinv == NULL means M = I.  tcol, h1: double[w].  v may not alias z or bg. */
+trplk_status trplk_inner_project(trplk_handle* h, int dtype, int64_t n, int64_t ld, int w,
+                                 const void* U, const void* BU, const void* z, const void* bg,
+                                 const void* dinv, double rho, void* v, double* tcol, double* h1);
+
+/* One classical Gram-Schmidt pass in the B-inner product: h = BU[:, 0:w]^T v
+ * (double[w]).  (Sec. 3: the basis G is kept B-orthonormal to [X, G].) */
+trplk_status trplk_project(trplk_handle* h, int dtype, int64_t n, int64_t ld, int w,
+                           const void* BU, const void* v, double* hout);
+
+/* CGS2 with B-normalisation (Sec. 3, the inner method's orthogonalisation):
+ *   v <- v - U h1, h2 = BU^T v, v <- v - U h2, Bv = B v, beta = sqrt(v^T B v)
+ * given h1 (double[w], from trplk_project or trplk_inner_project).  On
+ * return v holds the orthogonalised, NOT normalised vector, Bv its B-image
+ * (B == NULL: Bv may be NULL and Bv = v is implied), beta[0] = ||v||_B and
+ * beta[1] = the B-norm before orthogonalisation (by Pythagoras). */
+trplk_status trplk_cgs2(trplk_handle* h, int dtype, int64_t n, int64_t ld, int w, const void* U,
+                        const void* BU, const trplk_csr* B, const double* h1, void* v, void* Bv,
+                        double* beta);
+
+/* Rayleigh-Ritz on the w x w projection (Algorithm 1, 'compute eigenpairs of
+ * T'): T double, column-major (ldT), only the upper triangle is read.
+ * theta: double[w] ascending; Y: double w x w column-major (ld = w), each
+ * column signed so its largest-magnitude entry (first such) is positive.
+ * Cyclic Jacobi in one CTA, FP64.  w <= 64. */
+trplk_status trplk_rayleigh_ritz(trplk_handle* h, int w, const double* T, int ldT, double* theta,
+                                 double* Y);
+
+/* Thick-restart rotation (Algorithm 1, restart): Xout = U[:, 0:w] Y[:, 0:k]
+ * with Y double w x k column-major (ldY).  Xout: n x k (ld), must not alias U. */
+trplk_status trplk_rotate(trplk_handle* h, int dtype, int64_t n, int64_t ld, int w, int k,
+                          const void* U, const double* Y, int ldY, void* Xout);
+
+/* Residual norms from stored images: rnorm[i] = ||AX_i - theta_i BX_i||_2 and
+ * xnorm[i] = ||X_i||_2, i < k.  BX == NULL means B = I (BX = X). */
+trplk_status trplk_residual_norms(trplk_handle* h, int dtype, int64_t n, int64_t ld, int k,
+                                  const void* X, const void* AX, const void* BX,
+                                  const double* theta, double* rnorm, double* xnorm);
+
+/* The counter-based start block: X(i, c) = 2 u - 1, u the top 53 bits of one
+ * SplitMix64 step on state seed XOR (c n + i), for i < n, c < k; rows n..ld-1
+ * zero.  X: double, ld. */
+trplk_status trplk_start_block(trplk_handle* h, int64_t n, int64_t ld, int k, uint64_t seed,
+                               double* X);
+
+/* Final FP64 check (spec residual form): for i < p,
+ *   resid[i] = ||A x_i - theta_i B x_i||_2 / (normA ||x_i||_2)
+ * with fresh FP64 matvecs.  X double n x p (ld); A, B F64 on device
+ * (B == NULL: identity).  resid: double[p] (device). */
+trplk_status trplk_check_residuals(trplk_handle* h, const trplk_csr* A, const trplk_csr* B,
+                                   int64_t ld, int p, const double* X, const double* theta,
+                                   double normA, double* resid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRPLK_H_ */

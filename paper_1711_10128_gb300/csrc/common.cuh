@@ -1,0 +1,180 @@
+// Internal helpers shared by the CUDA translation units of libtrplk.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "trplk.h"
+
+namespace trplk {
+
+// ----------------------------------------------------------------- constants
+constexpr int kMaxQ = 64;          // largest supported basis size q
+constexpr int kMaxK = 32;          // largest supported thick-restart size p_hat
+constexpr int kMaxPartials = 1024; // CTA partial sums a reduction may hold
+
+// Error flags a kernel may raise in the device status word.
+enum : int {
+  kFlagTimeout = 1,     // a bounded wait on an mbarrier ran out
+  kFlagNaN = 2,         // a NaN/Inf reached a reduction
+  kFlagBreakdown = 4,   // Lanczos vector fell into the span of the basis
+  kFlagNotSPD = 8,      // x^T B x <= 0 seen
+  kFlagJacobi = 16,     // Rayleigh-Ritz eigensolver did not converge
+};
+
+// Storage traits.  Rows are tiled in TR-row tiles; a CTA has TR threads so a
+// thread owns one row of a tile.  One tile column is TR * sizeof(S) = 1 KiB.
+template <typename S> struct Tile;
+template <> struct Tile<double> { static constexpr int TR = 128; };
+template <> struct Tile<float> { static constexpr int TR = 256; };
+
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// ----------------------------------------------------------------- host errors
+struct Status {
+  trplk_status code = TRPLK_OK;
+  std::string msg;
+};
+
+#define TRPLK_CUDA_TRY(expr)                                                      \
+  do {                                                                            \
+    cudaError_t _e = (expr);                                                      \
+    if (_e != cudaSuccess) {                                                      \
+      char _b[512];                                                               \
+      snprintf(_b, sizeof(_b), "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), \
+               __FILE__, __LINE__);                                               \
+      throw ::trplk::Error(TRPLK_ECUDA, _b);                                      \
+    }                                                                             \
+  } while (0)
+
+struct Error {
+  trplk_status code;
+  std::string msg;
+  Error(trplk_status c, std::string m) : code(c), msg(std::move(m)) {}
+};
+
+inline void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    throw Error(TRPLK_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+// ----------------------------------------------------------------- device: compensated dot product
+// FP64-class accumulation of products of floats on the FP32 pipes (the FP64
+// pipe of this GPU runs at 1/58 of the FP32 rate).  This is Dot2 of Ogita,
+// Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26,
+// 2005): each product is split exactly into h + r by an FMA, h enters the
+// running sum p through Knuth's error-free TwoSum, and all rounding errors are
+// gathered in a second float s.  The value p + s is read out in FP64, so the
+// error is about (n u)^2 sum|a_i b_i| with u = 2^-24, n the terms per thread.
+// The _rn intrinsics keep the compiler from contracting these operations into
+// FMAs, which would break the error-free transforms.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  float t = __fadd_rn(a, b);
+  float bb = __fsub_rn(t, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bb)), __fsub_rn(b, bb));
+  s = t;
+}
+
+// ----------------------------------------------------------------- accumulators
+// Acc<S>: FP64-class accumulation of products of S values.
+template <typename S> struct Acc;
+template <> struct Acc<double> {
+  double v;
+  __device__ __forceinline__ void zero() { v = 0.0; }
+  __device__ __forceinline__ void fma(double a, double b) { v = ::fma(a, b, v); }
+  __device__ __forceinline__ void add(double a) { v += a; }
+  __device__ __forceinline__ double value() const { return v; }
+  __device__ __forceinline__ void shfl_down_add(int off) { v += __shfl_down_sync(0xffffffffu, v, off); }
+};
+template <> struct Acc<float> {
+  float p, s;
+  __device__ __forceinline__ void zero() { p = 0.f; s = 0.f; }
+  __device__ __forceinline__ void fma(float a, float b) {
+    float h = __fmul_rn(a, b);
+    float r = __fmaf_rn(a, b, -h);
+    float q;
+    two_sum(p, h, p, q);
+    s = __fadd_rn(s, __fadd_rn(q, r));
+  }
+  __device__ __forceinline__ void add(float a) {
+    float q;
+    two_sum(p, a, p, q);
+    s += q;
+  }
+  __device__ __forceinline__ double value() const { return (double)p + (double)s; }
+  __device__ __forceinline__ void shfl_down_add(int off) {
+    float po = __shfl_down_sync(0xffffffffu, p, off);
+    float so = __shfl_down_sync(0xffffffffu, s, off);
+    float q;
+    two_sum(p, po, p, q);
+    s += so + q;
+  }
+};
+
+// ----------------------------------------------------------------- device: mbarrier + bulk copy
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after `limit` polls (each poll itself suspends for a
+// hardware-chosen time) and reports false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit = 1u << 22) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+  }
+  return false;
+}
+
+// 1D bulk copy global -> shared (TMA engine), completion counted on `bar`.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// ----------------------------------------------------------------- device: grid reduction
+// Deterministic two-stage reduction: every CTA writes `n` partial values, the
+// last CTA to finish sums them in CTA order.  `counter` must be zero on entry
+// and is reset by the last CTA.  Returns true in the last CTA (all threads).
+__device__ __forceinline__ bool last_block_arrive(unsigned int* counter) {
+  __shared__ unsigned int s_ticket;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  bool last = (s_ticket == gridDim.x - 1);
+  if (last) __threadfence();
+  return last;
+}
+
+}  // namespace trplk

@@ -1,0 +1,79 @@
+// Host-side launch wrappers shared by the translation units of libtrplk.
+#pragma once
+#include "common.cuh"
+
+namespace trplk {
+
+// Per-handle device context: stream, SM count and the small scratch every
+// reduction kernel shares (kernels on one stream run one after another).
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 0;
+  double* partials = nullptr;      // [kMaxPartials][kPartialStride]
+  unsigned int* counter = nullptr; // last-CTA ticket, kept at zero between kernels
+  int* status = nullptr;           // device status word (kFlag*)
+};
+constexpr int kPartialStride = 2 * kMaxQ;
+
+// Device CSR in the library's own layout.
+template <typename S>
+struct DevCsr {
+  int64_t n = 0, nnz = 0;
+  const int64_t* rowptr = nullptr;
+  const int32_t* col = nullptr;
+  const S* val = nullptr;
+};
+
+// ---- SpMV (spmv.cu)
+// y = A x.
+template <typename S>
+void spmv(const Ctx& c, const DevCsr<S>& A, const S* x, S* y);
+// s = *scale; y = s (A x); g = s x; if bx: bg = s bx  (normalisation folded
+// into the next matvec).  Rows >= n of y, g, bg are left untouched.
+template <typename S>
+void spmv_scaled(const Ctx& c, const DevCsr<S>& A, const S* x, const double* scale, S* y, S* g,
+                 const S* bx, S* bg);
+
+// ---- tall-skinny passes (ts.cu).  All vectors have ld rows (zero padded).
+template <typename S>
+void ts_project(const Ctx& c, int64_t ld, int w, const S* BU, const S* v, double* hout);
+template <typename S>
+void ts_inner(const Ctx& c, int64_t ld, int w, const S* U, const S* BU, const S* z, const S* bg,
+              const S* dinv, int pmode, double rho, S* v, double* tcol, double* h1);
+template <typename S>
+void ts_update_project(const Ctx& c, int64_t ld, int w, const S* U, const S* BU, const double* h,
+                       S* v, double* hout);
+template <typename S>
+void ts_update_norm(const Ctx& c, int64_t ld, int w, const S* U, const double* h, const double* haux,
+                    S* v, double* beta2, double* scale, double eps_breakdown);
+template <typename S>
+void ts_update(const Ctx& c, int64_t ld, int w, const S* U, const double* h, S* v);
+template <typename S>
+void ts_dot_norm(const Ctx& c, int64_t ld, const S* v, const S* bv, const double* h1,
+                 const double* h2, int w, double* beta2, double* scale, double eps_breakdown);
+template <typename S>
+void ts_rotate(const Ctx& c, int64_t ld, int w, int k, const S* U, const double* Y, int ldY, S* X);
+template <typename S>
+void ts_resid(const Ctx& c, int64_t ld, int k, const S* X, const S* AX, const S* BX,
+              const double* theta, double* rnorm, double* xnorm);
+
+// ---- small kernels (misc.cu)
+// v = M (AX[:, t] - theta_t BX[:, t]); pmode PM_* ; theta_t read from device.
+template <typename S>
+void restart_vector(const Ctx& c, int64_t ld, const S* ax, const S* bx, const double* theta_t,
+                    const S* dinv, int pmode, S* v);
+template <typename D, typename S>
+void convert(const Ctx& c, int64_t count, const S* src, D* dst);
+void start_block(const Ctx& c, int64_t n, int64_t ld, int k, uint64_t seed, double* X);
+template <typename S>
+void jacobi_dinv(const Ctx& c, const DevCsr<S>& A, S* dinv);
+// r = x - rho * y   (elementwise, ld rows)
+template <typename S>
+void axpby_shift(const Ctx& c, int64_t ld, const S* x, const S* y, double rho, S* r);
+
+// ---- Rayleigh-Ritz (rr.cu): eigenpairs of the w x w symmetric T (upper
+// triangle read), theta ascending, Y (ld = w) sign-normalised.
+void rayleigh_ritz(const Ctx& c, int w, const double* T, int ldT, double* theta, double* Y);
+
+}  // namespace trplk

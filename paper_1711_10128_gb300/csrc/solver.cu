@@ -1,0 +1,835 @@
+// Host driver of TRPL+K (Algorithm 1 of Wu, Xue and Stathopoulos, Sec. 3) and
+// the C ABI of libtrplk.
+//
+// The cycle loop runs on the host and enqueues every vector operation on the
+// handle's stream; the only device->host traffic is a small read-back per
+// cycle (Ritz values, residual norms, Lanczos norms, status flags: under
+// 2 KB).  The projection T, the Ritz coefficients Y and all n-vectors stay in
+// device memory.  Storage type S is double (FP64 path) or float (FP32 phase
+// of the mixed path); coefficients, T, Ritz values and norms are always FP64.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "tallskinny.cuh"
+
+using namespace trplk;
+
+// ---------------------------------------------------------------- handle
+struct trplk_handle {
+  Ctx ctx;
+  bool own_stream = false;
+  std::string err;
+  struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+  };
+  std::map<std::string, Buf> bufs;
+  std::map<std::string, std::string> layouts;   // workspace group -> layout key
+  double* pinned = nullptr;   // host read-back area
+  size_t pinned_bytes = 0;
+
+  // A named device buffer of at least `bytes`, zero-filled when (re)allocated
+  // or when `zero` is set.
+  void* get(const std::string& name, size_t bytes, bool zero = false) {
+    bytes = std::max<size_t>(bytes, 256);
+    Buf& b = bufs[name];
+    if (b.bytes < bytes) {
+      if (b.p) cudaFree(b.p);
+      b.p = nullptr;
+      b.bytes = 0;
+      cudaError_t e = cudaMalloc(&b.p, bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(TRPLK_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes for " + name + " failed");
+      }
+      b.bytes = bytes;
+      TRPLK_CUDA_TRY(cudaMemsetAsync(b.p, 0, bytes, ctx.stream));
+    } else if (zero) {
+      TRPLK_CUDA_TRY(cudaMemsetAsync(b.p, 0, bytes, ctx.stream));
+    }
+    return b.p;
+  }
+  double* host(size_t count) {
+    size_t bytes = count * sizeof(double);
+    if (pinned_bytes < bytes) {
+      if (pinned) cudaFreeHost(pinned);
+      pinned = nullptr;
+      TRPLK_CUDA_TRY(cudaMallocHost(&pinned, bytes));
+      pinned_bytes = bytes;
+    }
+    return pinned;
+  }
+  void sync() { TRPLK_CUDA_TRY(cudaStreamSynchronize(ctx.stream)); }
+  int read_status() {
+    int s = 0;
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(&s, ctx.status, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+    sync();
+    return s;
+  }
+  void clear_status() { TRPLK_CUDA_TRY(cudaMemsetAsync(ctx.status, 0, sizeof(int), ctx.stream)); }
+};
+
+namespace {
+
+constexpr double kEpsBreakdown64 = 1e-12;
+constexpr double kEpsBreakdown32 = 1e-5;
+constexpr double kEpsDependent = 1e-10;
+
+trplk_status status_from_flags(int f) {
+  if (f & kFlagTimeout) return TRPLK_ETIMEOUT;
+  if (f & kFlagNaN) return TRPLK_NAN;
+  if (f & kFlagNotSPD) return TRPLK_NOT_SPD_B;
+  return TRPLK_OK;
+}
+
+void check_flags(trplk_handle* h, int mask_ignore = kFlagBreakdown) {
+  int f = h->read_status() & ~mask_ignore;
+  if (f) {
+    trplk_status s = status_from_flags(f);
+    if (s == TRPLK_OK) s = TRPLK_ECUDA;
+    throw Error(s, "device status flags 0x" + std::to_string(f));
+  }
+}
+
+// ---------------------------------------------------------------- device matrices
+struct Operator {
+  int64_t n = 0, nnz = 0;
+  DevCsr<double> d;   // FP64 values (always present)
+  DevCsr<float> f;    // FP32 values (mixed path only)
+  double norm1 = 0.0;
+};
+
+__global__ void validate_csr_kernel(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                                    int* status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = rowptr[i], b = rowptr[i + 1];
+    if (a > b || a < 0 || b > nnz) {
+      atomicOr(status, 64);
+      continue;
+    }
+    for (int64_t e = a; e < b; ++e)
+      if (col[e] < 0 || col[e] >= n) atomicOr(status, 64);
+  }
+}
+
+template <typename S>
+__global__ void row_abs_sum_kernel(int64_t n, const int64_t* rowptr, const S* val, double* out) {
+  // out[blockIdx.x] = max over the block's rows of sum_j |a_ij|
+  __shared__ double s_m[256];
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s += fabs((double)val[e]);
+    m = s > m ? s : m;
+  }
+  s_m[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s_m[threadIdx.x] = fmax(s_m[threadIdx.x], s_m[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = s_m[0];
+}
+
+__global__ void set_diag_block_kernel(double* T, int ldT, int k, const double* theta) {
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int j = e / k, i = e - j * k;
+    T[(int64_t)j * ldT + i] = (i == j) ? theta[i] : 0.0;
+  }
+}
+
+// Upload or wrap a caller's CSR; `tag` names the workspace slots.
+Operator make_operator(trplk_handle* h, const trplk_csr* M, const std::string& tag, bool need_f32) {
+  Operator op;
+  if (!M) return op;
+  if (M->n <= 0 || M->nnz < 0 || !M->rowptr || !M->col || !M->val)
+    throw Error(TRPLK_EINVAL, tag + ": empty or null CSR");
+  if (M->dtype != TRPLK_F64) throw Error(TRPLK_EINVAL, tag + ": solver matrices must have F64 values");
+  op.n = M->n;
+  op.nnz = M->nnz;
+  const Ctx& c = h->ctx;
+  if (M->on_device) {
+    op.d.rowptr = M->rowptr;
+    op.d.col = M->col;
+    op.d.val = static_cast<const double*>(M->val);
+  } else {
+    // host arrays: validate cheaply on the host, then copy
+    if (M->rowptr[0] != 0 || M->rowptr[M->n] != M->nnz) throw Error(TRPLK_EINVAL, tag + ": bad row pointers");
+    auto* rp = static_cast<int64_t*>(h->get(tag + ".rowptr", (M->n + 1) * sizeof(int64_t)));
+    auto* cl = static_cast<int32_t*>(h->get(tag + ".col", M->nnz * sizeof(int32_t)));
+    auto* vl = static_cast<double*>(h->get(tag + ".val", M->nnz * sizeof(double)));
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(rp, M->rowptr, (M->n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(cl, M->col, M->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream));
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(vl, M->val, M->nnz * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    op.d.rowptr = rp;
+    op.d.col = cl;
+    op.d.val = vl;
+  }
+  op.d.n = op.n;
+  op.d.nnz = op.nnz;
+  // structural validation on the device (column range, monotone rows)
+  h->clear_status();
+  validate_csr_kernel<<<std::max(1, std::min<int>((int)((op.n + 255) / 256), c.sms * 8)), 256, 0, c.stream>>>(
+      op.n, op.nnz, op.d.rowptr, op.d.col, c.status);
+  check_launch("validate_csr");
+  const int nb = std::max(1, std::min<int>((int)((op.n + 255) / 256), 1024));
+  auto* part = static_cast<double*>(h->get("norm1.part", 1024 * sizeof(double)));
+  row_abs_sum_kernel<double><<<nb, 256, 0, c.stream>>>(op.n, op.d.rowptr, op.d.val, part);
+  check_launch("row_abs_sum");
+  double* hp = h->host(1024);
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(hp, part, nb * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  int st = h->read_status();
+  if (st & 64) throw Error(TRPLK_EINVAL, tag + ": row pointers or column indices out of range");
+  op.norm1 = 0.0;
+  for (int i = 0; i < nb; ++i) op.norm1 = std::max(op.norm1, hp[i]);
+  if (need_f32) {
+    auto* vf = static_cast<float*>(h->get(tag + ".valf", op.nnz * sizeof(float)));
+    convert<float, double>(c, op.nnz, op.d.val, vf);
+    op.f = DevCsr<float>{op.n, op.nnz, op.d.rowptr, op.d.col, vf};
+  }
+  return op;
+}
+
+template <typename S> const DevCsr<S>& pick(const Operator& o);
+template <> const DevCsr<double>& pick<double>(const Operator& o) { return o.d; }
+template <> const DevCsr<float>& pick<float>(const Operator& o) { return o.f; }
+
+// ---------------------------------------------------------------- the solver
+struct SolveOut {
+  int cycles = 0;
+  int64_t mvA = 0, mvB = 0, prec = 0;
+  bool converged = false;
+  bool breakdown = false;
+  std::vector<double> theta;   // k Ritz values at exit
+  int cur = 0;                 // basis buffer holding X at exit
+};
+
+template <typename S>
+struct Solver {
+  trplk_handle* h;
+  const Ctx& c;
+  int64_t n, ld;
+  int p, q, k, l;
+  double tol;
+  int max_cycles;
+  bool hasB;
+  bool skip_converged;          // refinement phase: targets skip converged pairs
+  const Operator& Aop;
+  const Operator& Bop;
+  const DevCsr<S>& A;
+  const DevCsr<S>* B;
+  const S* dinv;
+  int pmode;
+  double normA;
+  double eps_breakdown;
+  // workspace
+  S* U[2];
+  S* AU[2];
+  S* BU[2];
+  S *v, *bv;
+  double *T, *theta, *Y, *h1, *h2, *betas, *scale, *rn, *xn;
+  int ldT;
+
+  Solver(trplk_handle* h_, const std::string& tag, int64_t n_, int p_, int q_, int k_, int l_, double tol_,
+         int maxc, const Operator& A_, const Operator& B_, bool hasB_, const S* dinv_, int pmode_)
+      : h(h_), c(h_->ctx), n(n_), p(p_), q(q_), k(k_), l(l_), tol(tol_), max_cycles(maxc), hasB(hasB_),
+        skip_converged(false), Aop(A_), Bop(B_), A(pick<S>(A_)), B(hasB_ ? &pick<S>(B_) : nullptr),
+        dinv(dinv_), pmode(pmode_) {
+    ld = round_up(n, 256);
+    normA = Aop.norm1;
+    eps_breakdown = sizeof(S) == 8 ? kEpsBreakdown64 : kEpsBreakdown32;
+    // Rows n..ld-1 of every n-vector must be zero.  Buffers are zeroed when
+    // first allocated and whenever the problem layout changes.
+    const std::string key = std::to_string(n) + "/" + std::to_string(q) + "/" + std::to_string(hasB);
+    const bool fresh = h->layouts[tag] != key;
+    h->layouts[tag] = key;
+    const size_t basis = (size_t)ld * q * sizeof(S);
+    for (int b = 0; b < 2; ++b) {
+      U[b] = static_cast<S*>(h->get(tag + ".U" + std::to_string(b), basis, fresh));
+      AU[b] = static_cast<S*>(h->get(tag + ".AU" + std::to_string(b), basis, fresh));
+      BU[b] = hasB ? static_cast<S*>(h->get(tag + ".BU" + std::to_string(b), basis, fresh)) : U[b];
+    }
+    v = static_cast<S*>(h->get(tag + ".v", ld * sizeof(S), fresh));
+    bv = hasB ? static_cast<S*>(h->get(tag + ".bv", ld * sizeof(S), fresh)) : v;
+    ldT = q;
+    T = static_cast<double*>(h->get(tag + ".T", (size_t)q * q * sizeof(double)));
+    theta = static_cast<double*>(h->get(tag + ".theta", kMaxQ * sizeof(double)));
+    Y = static_cast<double*>(h->get(tag + ".Y", (size_t)kMaxQ * kMaxQ * sizeof(double)));
+    h1 = static_cast<double*>(h->get(tag + ".h1", kMaxQ * sizeof(double)));
+    h2 = static_cast<double*>(h->get(tag + ".h2", kMaxQ * sizeof(double)));
+    betas = static_cast<double*>(h->get(tag + ".betas", 2 * (kMaxQ + 8) * sizeof(double)));
+    scale = static_cast<double*>(h->get(tag + ".scale", 8 * sizeof(double)));
+    rn = static_cast<double*>(h->get(tag + ".rn", kMaxQ * sizeof(double)));
+    xn = static_cast<double*>(h->get(tag + ".xn", kMaxQ * sizeof(double)));
+  }
+
+  S* col(S* M, int j) { return M + (size_t)j * ld; }
+
+  // v <- CGS2(v) against the w columns of (U, BU) given h1 = BU^T v; leaves
+  // v unnormalised, bv = B v, betas[slot] = (beta, beta0), *scale = 1/beta.
+  void orthonormalize_tail(int cur, int w, int slot, SolveOut& out) {
+    ts_update_project<S>(c, ld, w, U[cur], BU[cur], h1, v, h2);
+    if (hasB) {
+      ts_update<S>(c, ld, w, U[cur], h2, v);
+      spmv<S>(c, *B, v, bv);
+      out.mvB++;
+      ts_dot_norm<S>(c, ld, v, bv, h1, h2, w, betas + 2 * slot, scale, eps_breakdown);
+    } else {
+      ts_update_norm<S>(c, ld, w, U[cur], h2, h1, v, betas + 2 * slot, scale, eps_breakdown);
+    }
+  }
+
+  // normalise v into column w of (U, BU) and form column w of AU (one A matvec)
+  void append(int cur, int w, SolveOut& out) {
+    spmv_scaled<S>(c, A, v, scale, col(AU[cur], w), col(U[cur], w), hasB ? bv : nullptr,
+                   hasB ? col(BU[cur], w) : nullptr);
+    out.mvA++;
+  }
+
+  void read_back(int count, std::vector<double>& th, std::vector<double>& r, std::vector<double>& x,
+                 std::vector<double>* bet, int nbet) {
+    double* hp = h->host(4 * kMaxQ + 2 * (kMaxQ + 8));
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(hp, theta, count * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(hp + kMaxQ, rn, count * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(hp + 2 * kMaxQ, xn, count * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    if (bet && nbet > 0)
+      TRPLK_CUDA_TRY(cudaMemcpyAsync(hp + 4 * kMaxQ, betas, 2 * nbet * sizeof(double), cudaMemcpyDeviceToHost,
+                                     c.stream));
+    h->sync();
+    th.assign(hp, hp + count);
+    r.assign(hp + kMaxQ, hp + kMaxQ + count);
+    x.assign(hp + 2 * kMaxQ, hp + 2 * kMaxQ + count);
+    if (bet) bet->assign(hp + 4 * kMaxQ, hp + 4 * kMaxQ + 2 * nbet);
+  }
+
+  // Rayleigh-Ritz on T[0:w,0:w], rotate (U, AU, BU)[cur] into the other
+  // buffer, residual norms of the k new Ritz vectors.  Returns the new cur.
+  int rr_and_restart(int cur, int w) {
+    rayleigh_ritz(c, w, T, ldT, theta, Y);
+    const int nx = 1 - cur;
+    ts_rotate<S>(c, ld, w, k, U[cur], Y, w, U[nx]);
+    ts_rotate<S>(c, ld, w, k, AU[cur], Y, w, AU[nx]);
+    if (hasB) ts_rotate<S>(c, ld, w, k, BU[cur], Y, w, BU[nx]);
+    ts_resid<S>(c, ld, k, U[nx], AU[nx], hasB ? BU[nx] : nullptr, theta, rn, xn);
+    return nx;
+  }
+
+  // Algorithm 1.  X0: double n x k (ld) on the device.
+  SolveOut run(const double* X0) {
+    SolveOut out;
+    int cur = 0;
+    h->clear_status();
+    // start block into U[0][:, :k] (as S)
+    if (sizeof(S) == 8) {
+      TRPLK_CUDA_TRY(cudaMemcpyAsync(U[0], X0, (size_t)ld * k * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    } else {
+      convert<S, double>(c, (int64_t)ld * k, X0, U[0]);
+    }
+    // B-orthonormalise column by column (CGS2) and form A X (Algorithm 1 input)
+    for (int j = 0; j < k; ++j) {
+      TRPLK_CUDA_TRY(cudaMemcpyAsync(v, col(U[0], j), ld * sizeof(S), cudaMemcpyDeviceToDevice, c.stream));
+      ts_project<S>(c, ld, j, BU[0], v, h1);
+      orthonormalize_tail(0, j, j, out);
+      append(0, j, out);
+    }
+    // T = X^T A X (upper triangle), initial RR
+    for (int j = 0; j < k; ++j) ts_project<S>(c, ld, j + 1, U[0], col(AU[0], j), T + (size_t)j * ldT);
+    cur = rr_and_restart(0, k);
+    std::vector<double> th, r, x, bet;
+    read_back(k, th, r, x, &bet, k);
+    check_flags(h, kFlagBreakdown);
+    for (int j = 0; j < k; ++j)
+      if (!(bet[2 * j] > eps_breakdown * bet[2 * j + 1]))
+        throw Error(TRPLK_EINVAL, "start block is numerically rank deficient");
+
+    auto converged_vec = [&](const std::vector<double>& rr, const std::vector<double>& xx) {
+      std::vector<char> cv(k);
+      for (int i = 0; i < k; ++i) cv[i] = rr[i] <= tol * normA * xx[i];
+      return cv;
+    };
+    int t = 0;
+    if (skip_converged) {
+      auto cv = converged_vec(r, x);
+      while (t < p && cv[t]) ++t;
+      if (t >= p) {
+        out.converged = true;
+        out.theta = th;
+        out.cur = cur;
+        return out;
+      }
+    }
+    // X_prev: columns [xp_start, xp_start + xp_count) of U[xp_buf]
+    int xp_buf = -1, xp_start = 0, xp_count = 0;
+
+    for (int cycle = 1; cycle <= max_cycles; ++cycle) {
+      out.cycles = cycle;
+      const double rho = th[t];
+      h->clear_status();
+      set_diag_block_kernel<<<1, 256, 0, c.stream>>>(T, ldT, k, theta);
+      check_launch("set_diag_block");
+      // first Lanczos vector u = M (A x_t - rho B x_t)  (Algorithm 1, restart)
+      restart_vector<S>(c, ld, col(AU[cur], t), col(BU[cur], t), theta + t, dinv, pmode, v);
+      out.prec++;
+      ts_project<S>(c, ld, k, BU[cur], v, h1);
+      orthonormalize_tail(cur, k, 0, out);
+      const int nprev = (xp_buf >= 0) ? xp_count : 0;
+      const int m = q - k - nprev;
+      int w = k;
+      // inner preconditioned Lanczos with the T update (eq. (UpdateT))
+      for (int j = 0; j < m; ++j) {
+        append(cur, w, out);
+        ++w;
+        if (j < m - 1) {
+          ts_inner<S>(c, ld, w, U[cur], BU[cur], col(AU[cur], w - 1), col(BU[cur], w - 1), dinv, pmode, rho, v,
+                      T + (size_t)(w - 1) * ldT, h1);
+          out.prec++;
+          orthonormalize_tail(cur, w, j + 1, out);
+        } else {
+          ts_project<S>(c, ld, w, U[cur], col(AU[cur], w - 1), T + (size_t)(w - 1) * ldT);
+        }
+      }
+      // breakdown: find the first Lanczos norm that collapsed (slots 0..m-1)
+      {
+        double* hp = h->host(2 * (kMaxQ + 8));
+        TRPLK_CUDA_TRY(cudaMemcpyAsync(hp, betas, 2 * m * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        h->sync();
+        int good = m;
+        for (int j = 0; j < m; ++j)
+          if (!(hp[2 * j] > eps_breakdown * hp[2 * j + 1])) { good = j; break; }
+        if (good < m) {
+          out.breakdown = true;
+          w = k + good;
+          if (good == 0 && nprev == 0) {
+            out.theta = th;
+            out.cur = cur;
+            return out;
+          }
+        }
+      }
+      // +K: orthogonalise X_prev against [X, G] and complete T (Algorithm 1)
+      for (int i = 0; i < nprev; ++i) {
+        TRPLK_CUDA_TRY(cudaMemcpyAsync(v, col(U[xp_buf], xp_start + i), ld * sizeof(S), cudaMemcpyDeviceToDevice,
+                                       c.stream));
+        ts_project<S>(c, ld, w, BU[cur], v, h1);
+        orthonormalize_tail(cur, w, kMaxQ, out);
+        double* hp = h->host(2);
+        TRPLK_CUDA_TRY(cudaMemcpyAsync(hp, betas + 2 * kMaxQ, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        h->sync();
+        if (!(hp[0] > kEpsDependent)) continue;   // X_prev columns have unit B-norm
+        append(cur, w, out);
+        ++w;
+        ts_project<S>(c, ld, w, U[cur], col(AU[cur], w - 1), T + (size_t)(w - 1) * ldT);
+      }
+      // X_prev for the next cycle: x_t .. x_min(t+l-1, p) of this cycle's X
+      const int nxt_start = t, nxt_count = std::max(0, std::min(t + l, p) - t);
+      const int old = cur;
+      cur = rr_and_restart(cur, w);
+      read_back(k, th, r, x, nullptr, 0);
+      check_flags(h, kFlagBreakdown);
+      auto cv = converged_vec(r, x);
+      xp_buf = old;
+      xp_start = nxt_start;
+      xp_count = nxt_count;
+      if (cv[t]) {   // Algorithm 1: flag, drop x_1^prev, advance the target
+        ++t;
+        if (xp_count > 0) { ++xp_start; --xp_count; }
+        if (skip_converged) while (t < p && cv[t]) ++t;
+      }
+      if (t >= p) {
+        int fail = -1;
+        for (int i = 0; i < p; ++i)
+          if (!cv[i]) { fail = i; break; }
+        if (fail < 0) {
+          out.converged = true;
+          break;
+        }
+        t = fail;
+      }
+    }
+    out.theta = th;
+    out.cur = cur;
+    return out;
+  }
+};
+
+// Final FP64 check with fresh matvecs: resid[i] = ||A x - theta B x|| / (||A||_1 ||x||).
+void check_residuals_fp64(trplk_handle* h, const Operator& Aop, const Operator* Bop, int64_t ld, int p,
+                          const double* X, const double* theta_dev, double normA, double* resid_host) {
+  const Ctx& c = h->ctx;
+  double* ax = static_cast<double*>(h->get("check.ax", ld * sizeof(double), true));
+  double* bx = static_cast<double*>(h->get("check.bx", ld * sizeof(double), true));
+  double* rn = static_cast<double*>(h->get("check.rn", kMaxQ * sizeof(double)));
+  double* xn = static_cast<double*>(h->get("check.xn", kMaxQ * sizeof(double)));
+  for (int i = 0; i < p; ++i) {
+    const double* xi = X + (size_t)i * ld;
+    spmv<double>(c, Aop.d, xi, ax);
+    if (Bop) spmv<double>(c, Bop->d, xi, bx);
+    ts_resid<double>(c, ld, 1, xi, ax, Bop ? bx : nullptr, theta_dev + i, rn + i, xn + i);
+  }
+  double* hp = h->host(2 * kMaxQ);
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(hp, rn, p * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(hp + kMaxQ, xn, p * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  h->sync();
+  for (int i = 0; i < p; ++i) resid_host[i] = hp[i] / (normA * hp[kMaxQ + i]);
+}
+
+void validate_params(const trplk_params* P, int64_t n) {
+  if (!P) throw Error(TRPLK_EINVAL, "params is NULL");
+  if (P->which != TRPLK_SMALLEST) throw Error(TRPLK_EINVAL, "only which = TRPLK_SMALLEST is supported");
+  if (P->p < 1 || P->k < P->p) throw Error(TRPLK_EINVAL, "need 1 <= p <= k");
+  if (P->k > kMaxK) throw Error(TRPLK_EINVAL, "k (thick-restart size) must be <= 32");
+  if (P->l < 0) throw Error(TRPLK_EINVAL, "l must be >= 0");
+  if (P->q < P->k + std::max(P->l, 1) + 1) throw Error(TRPLK_EINVAL, "need q >= k + max(l,1) + 1");
+  if (P->q > kMaxQ) throw Error(TRPLK_EINVAL, "q must be <= 64");
+  if (P->q > n) throw Error(TRPLK_EINVAL, "q must be <= n");
+  if (!(P->tol > 0.0)) throw Error(TRPLK_EINVAL, "tol must be > 0");
+  if (P->max_cycles < 1) throw Error(TRPLK_EINVAL, "max_cycles must be >= 1");
+  if (P->precond < TRPLK_PRECOND_NONE || P->precond > TRPLK_PRECOND_JACOBI)
+    throw Error(TRPLK_EINVAL, "unsupported preconditioner");
+  if (P->precision != TRPLK_PRECISION_FP64 && P->precision != TRPLK_PRECISION_MIXED)
+    throw Error(TRPLK_EINVAL, "unknown precision");
+}
+
+template <typename F>
+trplk_status guarded(trplk_handle* h, F&& f) {
+  if (!h) return TRPLK_EINVAL;
+  h->err.clear();
+  try {
+    TRPLK_CUDA_TRY(cudaSetDevice(h->ctx.device));
+    return f();
+  } catch (const Error& e) {
+    h->err = e.msg;
+    if (e.code == TRPLK_ECUDA) cudaGetLastError();
+    return e.code;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return TRPLK_ECUDA;
+  }
+}
+
+DevCsr<double> dev_csr64(const trplk_csr* M) {
+  if (!M || !M->on_device) throw Error(TRPLK_EINVAL, "step-level calls take device CSR matrices");
+  if (M->dtype != TRPLK_F64) throw Error(TRPLK_EINVAL, "expected F64 values");
+  return DevCsr<double>{M->n, M->nnz, M->rowptr, M->col, static_cast<const double*>(M->val)};
+}
+
+void check_ld(int64_t n, int64_t ld) {
+  if (n < 1 || ld < n || ld % 256 != 0) throw Error(TRPLK_EINVAL, "need n >= 1, ld >= n, ld % 256 == 0");
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+int trplk_abi_version(void) { return TRPLK_ABI_VERSION; }
+
+trplk_status trplk_create(trplk_handle** out, int device, void* stream) {
+  if (!out) return TRPLK_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return TRPLK_EINVAL;
+  }
+  auto* h = new trplk_handle();
+  try {
+    h->ctx.device = device;
+    TRPLK_CUDA_TRY(cudaSetDevice(device));
+    TRPLK_CUDA_TRY(cudaDeviceGetAttribute(&h->ctx.sms, cudaDevAttrMultiProcessorCount, device));
+    if (stream) {
+      h->ctx.stream = static_cast<cudaStream_t>(stream);
+    } else {
+      TRPLK_CUDA_TRY(cudaStreamCreateWithFlags(&h->ctx.stream, cudaStreamNonBlocking));
+      h->own_stream = true;
+    }
+    h->ctx.partials = static_cast<double*>(h->get("ctx.partials", (size_t)kMaxPartials * kPartialStride * sizeof(double)));
+    h->ctx.counter = static_cast<unsigned int*>(h->get("ctx.counter", 64));
+    h->ctx.status = static_cast<int*>(h->get("ctx.status", 64));
+    h->sync();
+  } catch (const Error& e) {
+    trplk_destroy(h);
+    return e.code;
+  }
+  *out = h;
+  return TRPLK_OK;
+}
+
+trplk_status trplk_destroy(trplk_handle* h) {
+  if (!h) return TRPLK_OK;
+  cudaSetDevice(h->ctx.device);
+  if (h->ctx.stream) cudaStreamSynchronize(h->ctx.stream);
+  for (auto& kv : h->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  if (h->own_stream && h->ctx.stream) cudaStreamDestroy(h->ctx.stream);
+  delete h;
+  return TRPLK_OK;
+}
+
+const char* trplk_last_error(const trplk_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B, const trplk_params* P,
+                         const double* X0, double* evals, double* evecs, double* resid, trplk_info* info) {
+  return guarded(h, [&]() -> trplk_status {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!A) throw Error(TRPLK_EINVAL, "A is NULL");
+    if (!evals || !evecs || !resid) throw Error(TRPLK_EINVAL, "output pointer is NULL");
+    validate_params(P, A->n);
+    if (B && (B->n != A->n || B->on_device != A->on_device)) throw Error(TRPLK_EINVAL, "A and B differ in n or location");
+    const bool mixed = P->precision == TRPLK_PRECISION_MIXED;
+    const Ctx& c = h->ctx;
+    Operator Aop = make_operator(h, A, "A", mixed);
+    Operator Bop = make_operator(h, B, "B", mixed);
+    const bool hasB = B != nullptr;
+    const int64_t n = A->n, ld = round_up(n, 256);
+    // preconditioner
+    const int pmode = P->precond == TRPLK_PRECOND_JACOBI ? PM_JACOBI : PM_IDENTITY;
+    double* dinv64 = nullptr;
+    float* dinv32 = nullptr;
+    if (pmode == PM_JACOBI) {
+      dinv64 = static_cast<double*>(h->get("dinv64", ld * sizeof(double), true));
+      jacobi_dinv<double>(c, Aop.d, dinv64);
+      if (mixed) {
+        dinv32 = static_cast<float*>(h->get("dinv32", ld * sizeof(float), true));
+        convert<float, double>(c, ld, dinv64, dinv32);
+      }
+    }
+    // start block (double, ld)
+    double* X0d = static_cast<double*>(h->get("X0", (size_t)ld * P->k * sizeof(double), X0 != nullptr));
+    if (X0) {
+      TRPLK_CUDA_TRY(cudaMemcpy2DAsync(X0d, ld * sizeof(double), X0, n * sizeof(double), n * sizeof(double), P->k,
+                                       cudaMemcpyDefault, c.stream));
+    } else {
+      start_block(c, n, ld, P->k, P->seed, X0d);
+    }
+    trplk_info inf;
+    memset(&inf, 0, sizeof(inf));
+    inf.normA = Aop.norm1;
+    SolveOut res;
+    const double* Xfinal = nullptr;
+    const double* theta_dev = nullptr;
+    bool breakdown = false;
+    if (!mixed) {
+      Solver<double> S(h, "f64", n, P->p, P->q, P->k, P->l, P->tol, P->max_cycles, Aop, Bop, hasB, dinv64, pmode);
+      res = S.run(X0d);
+      inf.cycles = res.cycles;
+      inf.mv_A = res.mvA;
+      inf.mv_B = res.mvB;
+      inf.prec_apply = res.prec;
+      Xfinal = S.U[res.cur];
+      theta_dev = S.theta;
+      breakdown = res.breakdown && !res.converged;
+    } else {
+      const double tol32 = P->mixed_tol > 0.0 ? P->mixed_tol : 1e-6;
+      Solver<float> S32(h, "f32", n, P->p, P->q, P->k, P->l, std::max(tol32, P->tol), P->max_cycles, Aop, Bop, hasB,
+                        dinv32, pmode);
+      SolveOut r32 = S32.run(X0d);
+      // promote the k Ritz vectors and refine in FP64 from them
+      double* Xr = static_cast<double*>(h->get("Xrefine", (size_t)ld * P->k * sizeof(double)));
+      convert<double, float>(c, (int64_t)ld * P->k, S32.U[r32.cur], Xr);
+      Solver<double> S64(h, "f64", n, P->p, P->q, P->k, P->l, P->tol, std::max(1, P->max_cycles - r32.cycles), Aop,
+                         Bop, hasB, dinv64, pmode);
+      S64.skip_converged = true;
+      SolveOut r64 = S64.run(Xr);
+      inf.cycles = r32.cycles;
+      inf.refine_cycles = r64.cycles;
+      inf.mv_A = r32.mvA + r64.mvA;
+      inf.mv_B = r32.mvB + r64.mvB;
+      inf.prec_apply = r32.prec + r64.prec;
+      Xfinal = S64.U[r64.cur];
+      theta_dev = S64.theta;
+      res = r64;
+      breakdown = r64.breakdown && !r64.converged;
+    }
+    // final FP64 check with fresh matvecs
+    std::vector<double> rh(P->p);
+    check_residuals_fp64(h, Aop, hasB ? &Bop : nullptr, ld, P->p, Xfinal, theta_dev, Aop.norm1, rh.data());
+    inf.mv_check = (int64_t)P->p * (hasB ? 2 : 1);
+    inf.nconv = 0;
+    inf.max_resid = 0.0;
+    for (int i = 0; i < P->p; ++i) {
+      inf.nconv += rh[i] <= P->tol;
+      inf.max_resid = std::max(inf.max_resid, rh[i]);
+    }
+    // outputs
+    const cudaMemcpyKind k2o = P->outputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(evals, theta_dev, P->p * sizeof(double), k2o, c.stream));
+    TRPLK_CUDA_TRY(cudaMemcpy2DAsync(evecs, n * sizeof(double), Xfinal, ld * sizeof(double), n * sizeof(double), P->p,
+                                     k2o, c.stream));
+    if (P->outputs_on_device) {
+      TRPLK_CUDA_TRY(cudaMemcpyAsync(resid, rh.data(), P->p * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    } else {
+      memcpy(resid, rh.data(), P->p * sizeof(double));
+    }
+    h->sync();
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    if (inf.nconv == P->p) return TRPLK_OK;
+    if (breakdown) {
+      h->err = "Krylov space became invariant (breakdown)";
+      return TRPLK_BREAKDOWN;
+    }
+    h->err = "not converged within max_cycles";
+    return TRPLK_NOT_CONVERGED;
+  });
+}
+
+// ---------------------------------------------------------------- step-level entry points
+trplk_status trplk_spmv(trplk_handle* h, const trplk_csr* A, const void* x, void* y) {
+  return guarded(h, [&]() -> trplk_status {
+    if (!A || !A->on_device || !x || !y || A->n < 1) throw Error(TRPLK_EINVAL, "bad spmv arguments");
+    if (x == y) throw Error(TRPLK_EINVAL, "y must not alias x");
+    if (A->dtype == TRPLK_F64) {
+      spmv<double>(h->ctx, dev_csr64(A), static_cast<const double*>(x), static_cast<double*>(y));
+    } else if (A->dtype == TRPLK_F32) {
+      DevCsr<float> a{A->n, A->nnz, A->rowptr, A->col, static_cast<const float*>(A->val)};
+      spmv<float>(h->ctx, a, static_cast<const float*>(x), static_cast<float*>(y));
+    } else {
+      throw Error(TRPLK_EINVAL, "bad dtype");
+    }
+    h->sync();
+    return TRPLK_OK;
+  });
+}
+
+#define TRPLK_DISPATCH(dtype, ...)                                    \
+  do {                                                                \
+    if ((dtype) == TRPLK_F64) {                                       \
+      using S = double;                                               \
+      __VA_ARGS__;                                                    \
+    } else if ((dtype) == TRPLK_F32) {                                \
+      using S = float;                                                \
+      __VA_ARGS__;                                                    \
+    } else {                                                          \
+      throw Error(TRPLK_EINVAL, "bad dtype");                         \
+    }                                                                 \
+  } while (0)
+
+trplk_status trplk_inner_project(trplk_handle* h, int dtype, int64_t n, int64_t ld, int w, const void* U,
+                                 const void* BU, const void* z, const void* bg, const void* dinv, double rho,
+                                 void* v, double* tcol, double* h1) {
+  return guarded(h, [&]() -> trplk_status {
+    check_ld(n, ld);
+    if (w < 1 || w > kMaxQ || !U || !BU || !z || !bg || !v || !tcol || !h1) throw Error(TRPLK_EINVAL, "bad arguments");
+    h->clear_status();
+    TRPLK_DISPATCH(dtype, ts_inner<S>(h->ctx, ld, w, (const S*)U, (const S*)BU, (const S*)z, (const S*)bg,
+                                      (const S*)dinv, dinv ? PM_JACOBI : PM_IDENTITY, rho, (S*)v, tcol, h1));
+    check_flags(h, 0);
+    return TRPLK_OK;
+  });
+}
+
+trplk_status trplk_project(trplk_handle* h, int dtype, int64_t n, int64_t ld, int w, const void* BU, const void* v,
+                           double* hout) {
+  return guarded(h, [&]() -> trplk_status {
+    check_ld(n, ld);
+    if (w < 1 || w > kMaxQ || !BU || !v || !hout) throw Error(TRPLK_EINVAL, "bad arguments");
+    h->clear_status();
+    TRPLK_DISPATCH(dtype, ts_project<S>(h->ctx, ld, w, (const S*)BU, (const S*)v, hout));
+    check_flags(h, 0);
+    return TRPLK_OK;
+  });
+}
+
+trplk_status trplk_cgs2(trplk_handle* h, int dtype, int64_t n, int64_t ld, int w, const void* U, const void* BU,
+                        const trplk_csr* B, const double* h1, void* v, void* Bv, double* beta) {
+  return guarded(h, [&]() -> trplk_status {
+    check_ld(n, ld);
+    if (w < 0 || w > kMaxQ || !U || !BU || !v || !beta || (w > 0 && !h1)) throw Error(TRPLK_EINVAL, "bad arguments");
+    if (B && (!Bv || !B->on_device || B->dtype != dtype)) throw Error(TRPLK_EINVAL, "bad B arguments");
+    h->clear_status();
+    const Ctx& c = h->ctx;
+    double* h2 = static_cast<double*>(h->get("step.h2", kMaxQ * sizeof(double)));
+    double* sc = static_cast<double*>(h->get("step.scale", 8 * sizeof(double)));
+    TRPLK_DISPATCH(dtype, {
+      const double eps = sizeof(S) == 8 ? kEpsBreakdown64 : kEpsBreakdown32;
+      ts_update_project<S>(c, ld, w, (const S*)U, (const S*)BU, h1, (S*)v, h2);
+      if (B) {
+        DevCsr<S> b{B->n, B->nnz, B->rowptr, B->col, static_cast<const S*>(B->val)};
+        ts_update<S>(c, ld, w, (const S*)U, h2, (S*)v);
+        spmv<S>(c, b, (const S*)v, (S*)Bv);
+        ts_dot_norm<S>(c, ld, (const S*)v, (const S*)Bv, h1, h2, w, beta, sc, eps);
+      } else {
+        ts_update_norm<S>(c, ld, w, (const S*)U, h2, h1, (S*)v, beta, sc, eps);
+      }
+    });
+    check_flags(h, kFlagBreakdown);
+    return TRPLK_OK;
+  });
+}
+
+trplk_status trplk_rayleigh_ritz(trplk_handle* h, int w, const double* T, int ldT, double* theta, double* Y) {
+  return guarded(h, [&]() -> trplk_status {
+    if (w < 1 || w > kMaxQ || ldT < w || !T || !theta || !Y) throw Error(TRPLK_EINVAL, "bad arguments");
+    h->clear_status();
+    rayleigh_ritz(h->ctx, w, T, ldT, theta, Y);
+    check_flags(h, 0);
+    return TRPLK_OK;
+  });
+}
+
+trplk_status trplk_rotate(trplk_handle* h, int dtype, int64_t n, int64_t ld, int w, int k, const void* U,
+                          const double* Y, int ldY, void* Xout) {
+  return guarded(h, [&]() -> trplk_status {
+    check_ld(n, ld);
+    if (w < 1 || w > kMaxQ || k < 1 || k > kMaxK || ldY < w || !U || !Y || !Xout || U == Xout)
+      throw Error(TRPLK_EINVAL, "bad arguments");
+    h->clear_status();
+    TRPLK_DISPATCH(dtype, ts_rotate<S>(h->ctx, ld, w, k, (const S*)U, Y, ldY, (S*)Xout));
+    check_flags(h, 0);
+    return TRPLK_OK;
+  });
+}
+
+trplk_status trplk_residual_norms(trplk_handle* h, int dtype, int64_t n, int64_t ld, int k, const void* X,
+                                  const void* AX, const void* BX, const double* theta, double* rnorm, double* xnorm) {
+  return guarded(h, [&]() -> trplk_status {
+    check_ld(n, ld);
+    if (k < 1 || k > kMaxQ || !X || !AX || !theta || !rnorm || !xnorm) throw Error(TRPLK_EINVAL, "bad arguments");
+    h->clear_status();
+    TRPLK_DISPATCH(dtype, ts_resid<S>(h->ctx, ld, k, (const S*)X, (const S*)AX, (const S*)BX, theta, rnorm, xnorm));
+    check_flags(h, 0);
+    return TRPLK_OK;
+  });
+}
+
+trplk_status trplk_start_block(trplk_handle* h, int64_t n, int64_t ld, int k, uint64_t seed, double* X) {
+  return guarded(h, [&]() -> trplk_status {
+    check_ld(n, ld);
+    if (k < 1 || !X) throw Error(TRPLK_EINVAL, "bad arguments");
+    start_block(h->ctx, n, ld, k, seed, X);
+    h->sync();
+    return TRPLK_OK;
+  });
+}
+
+trplk_status trplk_check_residuals(trplk_handle* h, const trplk_csr* A, const trplk_csr* B, int64_t ld, int p,
+                                   const double* X, const double* theta, double normA, double* resid) {
+  return guarded(h, [&]() -> trplk_status {
+    if (!A || !X || !theta || !resid || p < 1 || p > kMaxQ) throw Error(TRPLK_EINVAL, "bad arguments");
+    check_ld(A->n, ld);
+    Operator Aop;
+    Aop.n = A->n;
+    Aop.d = dev_csr64(A);
+    Operator Bop;
+    if (B) {
+      Bop.n = B->n;
+      Bop.d = dev_csr64(B);
+    }
+    h->clear_status();
+    std::vector<double> rh(p);
+    check_residuals_fp64(h, Aop, B ? &Bop : nullptr, ld, p, X, theta, normA, rh.data());
+    TRPLK_CUDA_TRY(cudaMemcpy(resid, rh.data(), p * sizeof(double), cudaMemcpyHostToDevice));
+    check_flags(h, 0);
+    return TRPLK_OK;
+  });
+}
+
+}  // extern "C"

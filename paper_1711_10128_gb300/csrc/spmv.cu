@@ -1,0 +1,216 @@
+// Sparse matrix-vector products and small elementwise kernels.
+//
+// SpMV (eq. (UpdateT), z = A g): CSR-stream, one thread per row.  A CTA owns
+// 256 consecutive rows; it streams the values and column indices of those
+// rows into shared memory with coalesced loads (the rows are contiguous in
+// CSR, so the whole block is one contiguous range), then each thread forms its
+// row's dot product from shared memory, gathering x through the read-only
+// cache (for the stencil and FEM operators the gathered x lines are reused
+// from L1/L2 by the neighbouring rows).  No warp-shuffle reductions: on this
+// GPU a shuffle-and-add tree in FP64 costs more FP64 instructions than the
+// products themselves.  A block whose rows hold more nonzeros than the
+// shared-memory chunk is processed in chunks.
+#include "launch.h"
+#include "tallskinny.cuh"
+
+namespace trplk {
+
+namespace {
+constexpr int kRows = 256;
+template <typename S> struct Chunk;
+template <> struct Chunk<double> { static constexpr int CH = 4096; };   // 48 KiB of (val, col)
+template <> struct Chunk<float> { static constexpr int CH = 4096; };    // 32 KiB
+
+template <typename S, bool SCALED>
+__global__ void __launch_bounds__(kRows) spmv_kernel(int64_t n, const int64_t* __restrict__ rowptr,
+                                                     const int32_t* __restrict__ col,
+                                                     const S* __restrict__ val, const S* __restrict__ x,
+                                                     S* __restrict__ y, const double* __restrict__ scale,
+                                                     S* __restrict__ g, const S* __restrict__ bx,
+                                                     S* __restrict__ bg) {
+  constexpr int CH = Chunk<S>::CH;
+  extern __shared__ __align__(16) unsigned char sm[];
+  S* s_val = reinterpret_cast<S*>(sm);
+  int32_t* s_col = reinterpret_cast<int32_t*>(sm + CH * sizeof(S));
+  const int64_t r0 = (int64_t)blockIdx.x * kRows;
+  const int64_t r1 = r0 + kRows < n ? r0 + kRows : n;
+  const int64_t row = r0 + threadIdx.x;
+  const int64_t base = rowptr[r0];
+  const int64_t end = rowptr[r1];
+  const int64_t my_s = row < n ? rowptr[row] : end;
+  const int64_t my_e = row < n ? rowptr[row + 1] : end;
+  S sum = 0;
+  for (int64_t c0 = base; c0 < end; c0 += CH) {
+    const int64_t c1 = c0 + CH < end ? c0 + CH : end;
+    for (int64_t e = c0 + threadIdx.x; e < c1; e += kRows) {
+      s_val[e - c0] = val[e];
+      s_col[e - c0] = col[e];
+    }
+    __syncthreads();
+    const int64_t lo = my_s > c0 ? my_s : c0;
+    const int64_t hi = my_e < c1 ? my_e : c1;
+    for (int64_t e = lo; e < hi; ++e) sum = fmaS(s_val[e - c0], __ldg(&x[s_col[e - c0]]), sum);
+    __syncthreads();
+  }
+  if (row < n) {
+    if (SCALED) {
+      const S s = (S)(*scale);
+      y[row] = s * sum;
+      g[row] = s * x[row];
+      if (bx) bg[row] = s * bx[row];
+    } else {
+      y[row] = sum;
+    }
+  }
+}
+
+template <typename S>
+void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const double* scale, S* g,
+                 const S* bx, S* bg, bool scaled) {
+  if (A.n == 0) return;
+  constexpr int CH = Chunk<S>::CH;
+  const size_t smem = CH * (sizeof(S) + sizeof(int32_t));
+  const int64_t blocks = (A.n + kRows - 1) / kRows;
+  if (blocks > 0x7fffffff) throw Error(TRPLK_EINVAL, "matrix too large");
+  if (scaled) {
+    static bool cfg = false;
+    if (!cfg) { TRPLK_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); cfg = true; }
+    spmv_kernel<S, true><<<(unsigned)blocks, kRows, smem, c.stream>>>(A.n, A.rowptr, A.col, A.val, x, y, scale, g, bx, bg);
+  } else {
+    static bool cfg = false;
+    if (!cfg) { TRPLK_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); cfg = true; }
+    spmv_kernel<S, false><<<(unsigned)blocks, kRows, smem, c.stream>>>(A.n, A.rowptr, A.col, A.val, x, y, nullptr, nullptr, nullptr, nullptr);
+  }
+  check_launch("spmv_kernel");
+}
+
+// ---- elementwise kernels
+template <typename S>
+__global__ void restart_vector_kernel(int64_t ld, const S* __restrict__ ax, const S* __restrict__ bx,
+                                      const double* __restrict__ theta_t, const S* __restrict__ dinv,
+                                      int pmode, S* __restrict__ v) {
+  const S th = (S)(*theta_t);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ld; i += (int64_t)gridDim.x * blockDim.x) {
+    S r = ax[i] - th * bx[i];
+    if (pmode == PM_JACOBI) r *= dinv[i];
+    v[i] = r;
+  }
+}
+
+template <typename D, typename S>
+__global__ void convert_kernel(int64_t count, const S* __restrict__ src, D* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (D)src[i];
+}
+
+template <typename S>
+__global__ void axpby_shift_kernel(int64_t ld, const S* __restrict__ x, const S* __restrict__ y, double rho,
+                                   S* __restrict__ r) {
+  const S rr = (S)rho;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ld; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = x[i] - rr * y[i];
+}
+
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): one generator step on the state seed ^ counter.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t s) {
+  uint64_t z = s + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void start_block_kernel(int64_t n, int64_t ld, int k, uint64_t seed, double* __restrict__ X) {
+  const int64_t total = ld * (int64_t)k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / ld, i = e - c * ld;
+    double v = 0.0;
+    if (i < n) {
+      const uint64_t z = splitmix64(seed ^ (uint64_t)(c * n + i));
+      v = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+    }
+    X[e] = v;
+  }
+}
+
+template <typename S>
+__global__ void jacobi_dinv_kernel(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                   const S* __restrict__ val, S* __restrict__ dinv, int* status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    S d = 0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+      if (col[e] == i) d = val[e];
+    if (!(d != 0)) atomicOr(status, kFlagNaN);
+    dinv[i] = d != 0 ? (S)1 / d : (S)0;
+  }
+}
+
+inline unsigned grid_for(const Ctx& c, int64_t count) {
+  int64_t g = (count + 255) / 256;
+  int64_t cap = (int64_t)c.sms * 8;
+  return (unsigned)(g < cap ? (g > 0 ? g : 1) : cap);
+}
+
+}  // namespace
+
+template <typename S>
+void spmv(const Ctx& c, const DevCsr<S>& A, const S* x, S* y) {
+  spmv_launch<S>(c, A, x, y, nullptr, nullptr, nullptr, nullptr, false);
+}
+
+template <typename S>
+void spmv_scaled(const Ctx& c, const DevCsr<S>& A, const S* x, const double* scale, S* y, S* g,
+                 const S* bx, S* bg) {
+  spmv_launch<S>(c, A, x, y, scale, g, bx, bg, true);
+}
+
+template <typename S>
+void restart_vector(const Ctx& c, int64_t ld, const S* ax, const S* bx, const double* theta_t,
+                    const S* dinv, int pmode, S* v) {
+  restart_vector_kernel<S><<<grid_for(c, ld), 256, 0, c.stream>>>(ld, ax, bx, theta_t, dinv, pmode, v);
+  check_launch("restart_vector");
+}
+
+template <typename D, typename S>
+void convert(const Ctx& c, int64_t count, const S* src, D* dst) {
+  if (count == 0) return;
+  convert_kernel<D, S><<<grid_for(c, count), 256, 0, c.stream>>>(count, src, dst);
+  check_launch("convert");
+}
+
+void start_block(const Ctx& c, int64_t n, int64_t ld, int k, uint64_t seed, double* X) {
+  start_block_kernel<<<grid_for(c, ld * k), 256, 0, c.stream>>>(n, ld, k, seed, X);
+  check_launch("start_block");
+}
+
+template <typename S>
+void jacobi_dinv(const Ctx& c, const DevCsr<S>& A, S* dinv) {
+  jacobi_dinv_kernel<S><<<grid_for(c, A.n), 256, 0, c.stream>>>(A.n, A.rowptr, A.col, A.val, dinv, c.status);
+  check_launch("jacobi_dinv");
+}
+
+template <typename S>
+void axpby_shift(const Ctx& c, int64_t ld, const S* x, const S* y, double rho, S* r) {
+  axpby_shift_kernel<S><<<grid_for(c, ld), 256, 0, c.stream>>>(ld, x, y, rho, r);
+  check_launch("axpby_shift");
+}
+
+template void spmv<double>(const Ctx&, const DevCsr<double>&, const double*, double*);
+template void spmv<float>(const Ctx&, const DevCsr<float>&, const float*, float*);
+template void spmv_scaled<double>(const Ctx&, const DevCsr<double>&, const double*, const double*, double*,
+                                  double*, const double*, double*);
+template void spmv_scaled<float>(const Ctx&, const DevCsr<float>&, const float*, const double*, float*, float*,
+                                 const float*, float*);
+template void restart_vector<double>(const Ctx&, int64_t, const double*, const double*, const double*,
+                                     const double*, int, double*);
+template void restart_vector<float>(const Ctx&, int64_t, const float*, const float*, const double*, const float*,
+                                    int, float*);
+template void convert<float, double>(const Ctx&, int64_t, const double*, float*);
+template void convert<double, float>(const Ctx&, int64_t, const float*, double*);
+template void convert<double, double>(const Ctx&, int64_t, const double*, double*);
+template void jacobi_dinv<double>(const Ctx&, const DevCsr<double>&, double*);
+template void jacobi_dinv<float>(const Ctx&, const DevCsr<float>&, float*);
+template void axpby_shift<double>(const Ctx&, int64_t, const double*, const double*, double, double*);
+template void axpby_shift<float>(const Ctx&, int64_t, const float*, const float*, double, float*);
+
+}  // namespace trplk

@@ -1,0 +1,191 @@
+// Launchers of the tall-skinny streaming kernels (see tallskinny.cuh).
+#include <algorithm>
+#include <cstring>
+
+#include "launch.h"
+#include "tallskinny.cuh"
+
+namespace trplk {
+
+namespace {
+
+constexpr size_t kSmemMax = 232448 - 1024;   // opt-in shared memory per CTA less static use
+constexpr size_t kSmemPerSM = 233472;        // shared memory per SM
+
+template <typename S, int KIND>
+void launch_kind(const Ctx& c, TSArgs<S>& a, size_t smem, int grid) {
+  static bool configured = false;   // one attribute call per instantiation
+  if (!configured) {
+    TRPLK_CUDA_TRY(cudaFuncSetAttribute(ts_kernel<S, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kSmemMax));
+    configured = true;
+  }
+  ts_kernel<S, KIND><<<grid, Tile<S>::TR, smem, c.stream>>>(a);
+  check_launch("ts_kernel");
+}
+
+template <typename S>
+void run(const Ctx& c, TSArgs<S> a, int kind) {
+  constexpr int TR = Tile<S>::TR;
+  if (a.ld % TR != 0) throw Error(TRPLK_EINVAL, "leading dimension must be a multiple of 256");
+  if (a.w < 0 || a.w > kMaxQ) throw Error(TRPLK_EINVAL, "basis width out of range");
+  a.ntiles = (int)(a.ld / TR);
+  if (a.ntiles == 0) return;
+  const size_t fixed = ts_smem_fixed<S>(a.w, a.k);
+  const size_t stage = (size_t)(a.nmat * a.w + a.nvec) * TR * sizeof(S);
+  int stages = stage == 0 ? 1 : (int)std::min<size_t>(4, (kSmemMax - fixed) / stage);
+  if (stages < 1) throw Error(TRPLK_EINVAL, "tile does not fit in shared memory");
+  a.stages = stages;
+  const size_t smem = fixed + (size_t)stages * stage;
+  int per_sm = (int)std::max<size_t>(1, kSmemPerSM / (smem + 1024));
+  per_sm = std::min(per_sm, 2048 / TR);
+  int grid = std::min<int64_t>(a.ntiles, (int64_t)c.sms * per_sm);
+  grid = std::min(grid, kMaxPartials);
+  a.partials = c.partials;
+  a.pstride = kPartialStride;
+  a.counter = c.counter;
+  a.status = c.status;
+  a.kind = kind;
+  switch (kind) {
+    case TS_PROJ: launch_kind<S, TS_PROJ>(c, a, smem, grid); break;
+    case TS_INNER: launch_kind<S, TS_INNER>(c, a, smem, grid); break;
+    case TS_UPDPROJ: launch_kind<S, TS_UPDPROJ>(c, a, smem, grid); break;
+    case TS_UPDNORM: launch_kind<S, TS_UPDNORM>(c, a, smem, grid); break;
+    case TS_UPD: launch_kind<S, TS_UPD>(c, a, smem, grid); break;
+    case TS_ROT: launch_kind<S, TS_ROT>(c, a, smem, grid); break;
+    case TS_RESID: launch_kind<S, TS_RESID>(c, a, smem, grid); break;
+    case TS_DOT: launch_kind<S, TS_DOT>(c, a, smem, grid); break;
+    default: throw Error(TRPLK_EINVAL, "unknown tall-skinny kind");
+  }
+}
+
+template <typename S>
+TSArgs<S> blank() {
+  TSArgs<S> a;
+  memset(&a, 0, sizeof(a));
+  a.matsel[0] = 0;
+  a.matsel[1] = 0;
+  a.matsel[2] = 0;
+  return a;
+}
+
+}  // namespace
+
+template <typename S>
+void ts_project(const Ctx& c, int64_t ld, int w, const S* BU, const S* v, double* hout) {
+  if (w == 0) return;
+  TSArgs<S> a = blank<S>();
+  a.mat[0] = BU; a.nmat = 1;
+  a.vec[0] = v; a.nvec = 1;
+  a.w = w; a.ld = ld; a.out0 = hout;
+  run(c, a, TS_PROJ);
+}
+
+template <typename S>
+void ts_inner(const Ctx& c, int64_t ld, int w, const S* U, const S* BU, const S* z, const S* bg,
+              const S* dinv, int pmode, double rho, S* v, double* tcol, double* h1) {
+  TSArgs<S> a = blank<S>();
+  a.mat[0] = U;
+  if (BU == U) { a.nmat = 1; a.matsel[1] = 0; }
+  else { a.mat[1] = BU; a.nmat = 2; a.matsel[1] = 1; }
+  a.vec[0] = z;
+  if (pmode == PM_GIVEN) { a.vec[1] = v; a.nvec = 2; }
+  else {
+    a.vec[1] = bg;
+    a.nvec = 2;
+    if (pmode == PM_JACOBI) { a.vec[2] = dinv; a.nvec = 3; }
+  }
+  a.pmode = pmode; a.rho = rho; a.vout = v;
+  a.w = w; a.ld = ld; a.out0 = tcol; a.out1 = h1;
+  run(c, a, TS_INNER);
+}
+
+template <typename S>
+void ts_update_project(const Ctx& c, int64_t ld, int w, const S* U, const S* BU, const double* h,
+                       S* v, double* hout) {
+  TSArgs<S> a = blank<S>();
+  a.mat[0] = U;
+  if (BU == U) { a.nmat = 1; a.matsel[1] = 0; }
+  else { a.mat[1] = BU; a.nmat = 2; a.matsel[1] = 1; }
+  a.vec[0] = v; a.nvec = 1;
+  a.hcoef = h; a.vout = v;
+  a.w = w; a.ld = ld; a.out0 = hout;
+  run(c, a, TS_UPDPROJ);
+}
+
+template <typename S>
+void ts_update_norm(const Ctx& c, int64_t ld, int w, const S* U, const double* h, const double* haux,
+                    S* v, double* beta2, double* scale, double eps_breakdown) {
+  TSArgs<S> a = blank<S>();
+  a.mat[0] = U; a.nmat = w > 0 ? 1 : 0;
+  a.vec[0] = v; a.nvec = 1;
+  a.hcoef = w > 0 ? h : nullptr; a.haux = w > 0 ? haux : nullptr; a.vout = v;
+  a.w = w; a.ld = ld; a.out0 = beta2; a.scale_out = scale; a.eps_breakdown = eps_breakdown;
+  run(c, a, TS_UPDNORM);
+}
+
+template <typename S>
+void ts_update(const Ctx& c, int64_t ld, int w, const S* U, const double* h, S* v) {
+  if (w == 0) return;
+  TSArgs<S> a = blank<S>();
+  a.mat[0] = U; a.nmat = 1;
+  a.vec[0] = v; a.nvec = 1;
+  a.hcoef = h; a.vout = v;
+  a.w = w; a.ld = ld;
+  run(c, a, TS_UPD);
+}
+
+template <typename S>
+void ts_dot_norm(const Ctx& c, int64_t ld, const S* v, const S* bv, const double* h1,
+                 const double* h2, int w, double* beta2, double* scale, double eps_breakdown) {
+  TSArgs<S> a = blank<S>();
+  a.nmat = 0;
+  a.vec[0] = v; a.vec[1] = bv; a.nvec = 2;
+  a.w = w; a.ld = ld; a.hcoef = w > 0 ? h2 : nullptr; a.haux = w > 0 ? h1 : nullptr;
+  a.out0 = beta2; a.scale_out = scale; a.eps_breakdown = eps_breakdown;
+  run(c, a, TS_DOT);
+}
+
+template <typename S>
+void ts_rotate(const Ctx& c, int64_t ld, int w, int k, const S* U, const double* Y, int ldY, S* X) {
+  if (k > kMaxK) throw Error(TRPLK_EINVAL, "rotation width exceeds 32");
+  TSArgs<S> a = blank<S>();
+  a.mat[0] = U; a.nmat = 1;
+  a.nvec = 0;
+  a.Y = Y; a.ldY = ldY; a.k = k; a.xout = X;
+  a.w = w; a.ld = ld;
+  run(c, a, TS_ROT);
+}
+
+template <typename S>
+void ts_resid(const Ctx& c, int64_t ld, int k, const S* X, const S* AX, const S* BX,
+              const double* theta, double* rnorm, double* xnorm) {
+  TSArgs<S> a = blank<S>();
+  a.mat[0] = X; a.mat[1] = AX; a.matsel[0] = 0; a.matsel[1] = 1;
+  if (BX == nullptr || BX == X) { a.nmat = 2; a.matsel[2] = 0; }
+  else { a.mat[2] = BX; a.nmat = 3; a.matsel[2] = 2; }
+  a.nvec = 0;
+  a.theta = theta; a.k = k;
+  a.w = k; a.ld = ld; a.out0 = rnorm; a.out1 = xnorm;
+  run(c, a, TS_RESID);
+}
+
+#define TRPLK_INST(S)                                                                                 \
+  template void ts_project<S>(const Ctx&, int64_t, int, const S*, const S*, double*);                 \
+  template void ts_inner<S>(const Ctx&, int64_t, int, const S*, const S*, const S*, const S*,         \
+                            const S*, int, double, S*, double*, double*);                             \
+  template void ts_update_project<S>(const Ctx&, int64_t, int, const S*, const S*, const double*, S*, \
+                                     double*);                                                        \
+  template void ts_update_norm<S>(const Ctx&, int64_t, int, const S*, const double*, const double*,   \
+                                  S*, double*, double*, double);                                      \
+  template void ts_update<S>(const Ctx&, int64_t, int, const S*, const double*, S*);                  \
+  template void ts_dot_norm<S>(const Ctx&, int64_t, const S*, const S*, const double*, const double*, \
+                               int, double*, double*, double);                                        \
+  template void ts_rotate<S>(const Ctx&, int64_t, int, int, const S*, const double*, int, S*);        \
+  template void ts_resid<S>(const Ctx&, int64_t, int, const S*, const S*, const S*, const double*,    \
+                            double*, double*);
+
+TRPLK_INST(double)
+TRPLK_INST(float)
+
+}  // namespace trplk

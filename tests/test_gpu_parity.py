@@ -1,0 +1,429 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Step-level tests compare each kernel with the oracle's step on the same seeded
+inputs, element by element, at sizes that span several 256-row tiles plus a
+ragged tail.  Solve-level tests compare Ritz values with the oracle's after
+one and two cycles (same arithmetic up to rounding order), converged
+eigenvalues with the oracle and closed forms, and check B-orthonormality,
+residuals (recomputed by the oracle's own matvec) and the matvec accounting.
+
+Tolerances: FP64 kernels 1e-12 relative to the natural scale of the quantity
+(rounding-order differences of sums of <= n terms, n <= 10^5); FP32 storage
+kernels compare with the oracle evaluated on the same float inputs, with the
+compensated (Dot2) accumulations held to 1e-12 and FP32 arithmetic to 1e-6;
+converged eigenvalues 1e-10 relative (the required FP64 parity).
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import trplk as O
+from paper_1711_10128_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_10128_gb300 import build
+    build.build()
+    from paper_1711_10128_gb300 import binding as b
+    return b
+
+
+@pytest.fixture(scope="module")
+def h(lib):
+    hd = lib.Handle(0)
+    yield hd
+    hd.close()
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def dev_csr(lib, A, dtype=torch.float64):
+    rp, cl, vl = dev(A.rowptr), dev(A.col), dev(A.val, dtype)
+    return lib.make_csr(rp, cl, vl)
+
+
+def padded(X, ld, dtype=torch.float64):
+    """column-major (ld x k) device block from an n x k numpy array."""
+    n, k = X.shape
+    out = torch.zeros((k, ld), dtype=dtype, device="cuda")
+    out[:, :n] = torch.from_numpy(np.ascontiguousarray(X.T)).to(dtype).cuda()
+    return out
+
+
+def ld_of(n):
+    return (n + 255) // 256 * 256
+
+
+OPS = {
+    "lap2d_37": lambda: W.laplacian_2d(37),                                   # n = 1369, ragged
+    "diff3d_13": lambda: W.diffusion_3d(13, W.lognormal_field(13, 1.0, 3)),   # n = 2197
+    "fem_7": lambda: W.fem_q1_pencil(7, np.random.default_rng(4).uniform(1, 10, (7, 7, 7)))[0],
+}
+
+
+# ---------------------------------------------------------------- a1 SpMV
+@pytest.mark.parametrize("name", sorted(OPS))
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_spmv_matches_oracle(lib, h, name, prec):
+    A = OPS[name]()
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(A.n)
+    As = A.to_scipy()
+    if prec == "f64":
+        Ad = dev_csr(lib, A)
+        y = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        lib.trplk_spmv(h, Ad, dev(x), y)
+        ref = O.spmv(As, x)
+        scale = abs(As) @ np.abs(x)
+        assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-14 * scale + 1e-300)
+    else:
+        xf = x.astype(np.float32)
+        Af = sp.csr_matrix((A.val.astype(np.float32).astype(np.float64), A.col, A.rowptr), shape=(A.n, A.n))
+        Ad = dev_csr(lib, A, torch.float32)
+        y = torch.zeros(A.n, dtype=torch.float32, device="cuda")
+        lib.trplk_spmv(h, Ad, dev(xf), y)
+        ref = O.spmv(Af, xf.astype(np.float64))
+        scale = abs(Af) @ np.abs(xf.astype(np.float64))
+        assert np.all(np.abs(y.cpu().numpy().astype(np.float64) - ref) <= 1e-6 * scale)
+
+
+def test_spmv_full_size_sampled_rows(lib, h):
+    """128^3 lognormal diffusion (n = 2,097,152): sampled rows against the
+    oracle's row dot products."""
+    A = W.diffusion_3d(128, W.lognormal_field(128, 1.0, 1))
+    x = W.start_block(A.n, 1, 11)[:, 0]
+    y = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    lib.trplk_spmv(h, dev_csr(lib, A), dev(x), y)
+    yh = y.cpu().numpy()
+    rows = np.random.default_rng(2).choice(A.n, 4000, replace=False)
+    rows = np.concatenate([rows, [0, A.n - 1]])
+    for i in rows:
+        s, e = A.rowptr[i], A.rowptr[i + 1]
+        ref = float(np.dot(A.val[s:e], x[A.col[s:e]]))
+        assert abs(yh[i] - ref) <= 1e-14 * float(np.dot(np.abs(A.val[s:e]), np.abs(x[A.col[s:e]])))
+
+
+# ---------------------------------------------------------------- a2-a4 inner step
+def basis(n, w, seed, B=None):
+    Bf = (lambda v: v.copy()) if B is None else (lambda v: B @ v)
+    U, BU, _ = O.b_orthonormalise(np.random.default_rng(seed).standard_normal((n, w)), Bf)
+    return U, BU, Bf
+
+
+@pytest.mark.parametrize("n,w", [(1369, 1), (2197, 9), (5000, 40), (777, 64)])
+def test_inner_project_fp64(lib, h, n, w):
+    rng = np.random.default_rng(n + w)
+    U, BU, _ = basis(n, w, 3)
+    z, bg = rng.standard_normal(n), rng.standard_normal(n)
+    dinv = 1.0 / rng.uniform(1, 5, n)
+    rho = 0.37
+    ld = ld_of(n)
+    Ud = padded(U, ld)
+    zd, bgd, dvd = padded(z[:, None], ld), padded(bg[:, None], ld), padded(dinv[:, None], ld)
+    v = torch.zeros(ld, dtype=torch.float64, device="cuda")
+    tcol = torch.zeros(w, dtype=torch.float64, device="cuda")
+    h1 = torch.zeros(w, dtype=torch.float64, device="cuda")
+    lib.trplk_inner_project(h, lib.F64, n, ld, w, Ud, Ud, zd, bgd, dvd, rho, v, tcol, h1)
+    vref = dinv * (z - rho * bg)                     # the oracle's Jacobi step
+    # the GPU forms z - rho*bg with one FMA: a few ulp of |z| + |rho bg|
+    assert np.all(np.abs(v.cpu().numpy()[:n] - vref) <= 4e-16 * dinv * (np.abs(z) + rho * np.abs(bg)))
+    assert np.all(v.cpu().numpy()[n:] == 0)
+    sc = math.sqrt(n)
+    assert np.allclose(tcol.cpu().numpy(), U.T @ z, rtol=0, atol=1e-13 * sc)
+    assert np.allclose(h1.cpu().numpy(), U.T @ vref, rtol=0, atol=1e-13 * sc)
+
+
+@pytest.mark.parametrize("n,w", [(2197, 9), (5000, 40)])
+def test_inner_project_fp32_compensated(lib, h, n, w):
+    rng = np.random.default_rng(7)
+    U = rng.standard_normal((n, w)).astype(np.float32)
+    z = rng.standard_normal(n).astype(np.float32)
+    bg = rng.standard_normal(n).astype(np.float32)
+    ld = ld_of(n)
+    Ud = padded(U, ld, torch.float32)
+    zd, bgd = padded(z[:, None], ld, torch.float32), padded(bg[:, None], ld, torch.float32)
+    v = torch.zeros(ld, dtype=torch.float32, device="cuda")
+    tcol = torch.zeros(w, dtype=torch.float64, device="cuda")
+    h1 = torch.zeros(w, dtype=torch.float64, device="cuda")
+    rho = 0.25
+    lib.trplk_inner_project(h, lib.F32, n, ld, w, Ud, Ud, zd, bgd, None, rho, v, tcol, h1)
+    vh = v.cpu().numpy()[:n]
+    vref = (z - np.float32(rho) * bg)                # float arithmetic as on the GPU
+    assert np.allclose(vh, vref, rtol=1e-6, atol=1e-6)
+    U64 = U.astype(np.float64)
+    # exact products of the float data, summed in FP64: the compensated sums
+    # must agree to FP64 level relative to sum |u z|
+    exact_t = U64.T @ z.astype(np.float64)
+    mag = np.abs(U64).T @ np.abs(z.astype(np.float64))
+    assert np.all(np.abs(tcol.cpu().numpy() - exact_t) <= 1e-12 * mag)
+    exact_h = U64.T @ vh.astype(np.float64)
+    magh = np.abs(U64).T @ np.abs(vh.astype(np.float64))
+    assert np.all(np.abs(h1.cpu().numpy() - exact_h) <= 1e-12 * magh)
+
+
+@pytest.mark.parametrize("withB", [False, True])
+@pytest.mark.parametrize("w", [0, 1, 12, 30])
+def test_cgs2_matches_oracle(lib, h, withB, w):
+    if withB:
+        A, B = W.fem_q1_pencil(9)
+        Bs = B.to_scipy()
+        n = B.n
+    else:
+        n = 3001
+        Bs = None
+    U, BU, Bf = basis(n, max(w, 1), 5, Bs)
+    U, BU = U[:, :w], BU[:, :w]
+    x = np.random.default_rng(9).standard_normal(n)
+    wo, Bw, beta, beta0, hsum = O.cgs2(x, U, BU, Bf)
+    ld = ld_of(n)
+    if w:
+        Ud = padded(U, ld)
+        BUd = padded(BU, ld) if withB else Ud
+    else:
+        Ud = torch.zeros(ld, dtype=torch.float64, device="cuda")
+        BUd = Ud
+    v = padded(x[:, None], ld)[0].contiguous()
+    h1 = torch.from_numpy(BU.T @ x if w else np.zeros(1)).cuda()
+    bv = torch.zeros(ld, dtype=torch.float64, device="cuda")
+    bet = torch.zeros(2, dtype=torch.float64, device="cuda")
+    Bd = dev_csr(lib, B) if withB else None
+    lib.trplk_cgs2(h, lib.F64, n, ld, w, Ud, BUd, Bd, h1, v, bv if withB else None, bet)
+    vh = v.cpu().numpy()
+    assert np.allclose(vh[:n], wo, rtol=0, atol=1e-13 * np.abs(x).max())
+    assert np.all(vh[n:] == 0)
+    b = bet.cpu().numpy()
+    assert abs(b[0] - beta) <= 1e-12 * beta
+    assert abs(b[1] - beta0) <= 1e-12 * beta0
+    if withB:
+        assert np.allclose(bv.cpu().numpy()[:n], Bw, rtol=0, atol=1e-13 * np.abs(Bw).max())
+
+
+# ---------------------------------------------------------------- a6 Rayleigh-Ritz
+@pytest.mark.parametrize("w", [1, 2, 3, 17, 40, 64])
+def test_rayleigh_ritz_matches_oracle(lib, h, w):
+    rng = np.random.default_rng(w)
+    M = rng.standard_normal((w, w))
+    M = M + M.T + np.diag(np.arange(w) * 0.5)   # well separated spectrum
+    T = np.triu(M) + np.tril(rng.standard_normal((w, w)), -1) * 1e3   # lower triangle must be ignored
+    th_ref, Y_ref = O.rayleigh_ritz(np.triu(M))
+    Td = torch.from_numpy(np.asfortranarray(T).ravel(order="F")).cuda()
+    th = torch.zeros(w, dtype=torch.float64, device="cuda")
+    Y = torch.zeros(w * w, dtype=torch.float64, device="cuda")
+    lib.trplk_rayleigh_ritz(h, w, Td, w, th, Y)
+    scale = np.abs(th_ref).max()
+    assert np.allclose(th.cpu().numpy(), th_ref, rtol=0, atol=1e-13 * scale)
+    Yh = Y.cpu().numpy().reshape(w, w).T          # column-major
+    assert np.allclose(Yh, Y_ref, atol=1e-10)
+    assert np.allclose(Yh.T @ Yh, np.eye(w), atol=1e-13)
+
+
+def test_rayleigh_ritz_diagonal_and_degenerate(lib, h):
+    """Already-diagonal T (the state right after a thick restart) and an exactly
+    degenerate pair: eigenvalues exact, eigenvectors orthonormal."""
+    w = 12
+    d = np.array([3.0, 1.0, 2.0, 2.0, 5.0, -1.0, 0.5, 7.0, 7.0, 7.0, 4.0, 6.0])
+    T = np.diag(d)
+    th = torch.zeros(w, dtype=torch.float64, device="cuda")
+    Y = torch.zeros(w * w, dtype=torch.float64, device="cuda")
+    lib.trplk_rayleigh_ritz(h, w, torch.from_numpy(T.ravel(order="F")).cuda(), w, th, Y)
+    assert np.array_equal(th.cpu().numpy(), np.sort(d))
+    Yh = Y.cpu().numpy().reshape(w, w).T
+    assert np.allclose(Yh.T @ Yh, np.eye(w), atol=0)
+    assert np.allclose(T @ Yh, Yh * th.cpu().numpy(), atol=0)
+
+
+# ---------------------------------------------------------------- a7 rotation + residuals
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_rotate_and_residual_norms(lib, h, prec):
+    n, w, k = 4099, 33, 15
+    rng = np.random.default_rng(12)
+    U = rng.standard_normal((n, w))
+    AU = rng.standard_normal((n, w))
+    Yc = np.linalg.qr(rng.standard_normal((w, w)))[0]
+    theta = np.sort(rng.uniform(0, 2, k))
+    ld = ld_of(n)
+    dt, dtn = (torch.float64, np.float64) if prec == "f64" else (torch.float32, np.float32)
+    code = lib.F64 if prec == "f64" else lib.F32
+    Ud, AUd = padded(U, ld, dt), padded(AU, ld, dt)
+    Yd = torch.from_numpy(Yc.ravel(order="F")).cuda()
+    X = torch.zeros((k, ld), dtype=dt, device="cuda")
+    AX = torch.zeros((k, ld), dtype=dt, device="cuda")
+    lib.trplk_rotate(h, code, n, ld, w, k, Ud, Yd, w, X)
+    lib.trplk_rotate(h, code, n, ld, w, k, AUd, Yd, w, AX)
+    Uq, AUq = U.astype(dtn).astype(np.float64), AU.astype(dtn).astype(np.float64)
+    Xref, AXref = Uq @ Yc[:, :k], AUq @ Yc[:, :k]
+    tol = 1e-13 if prec == "f64" else 2e-6
+    assert np.allclose(X.cpu().numpy()[:, :n].T, Xref, rtol=0, atol=tol * np.abs(Uq).max() * math.sqrt(w))
+    assert np.all(X.cpu().numpy()[:, n:] == 0)
+    rn = torch.zeros(k, dtype=torch.float64, device="cuda")
+    xn = torch.zeros(k, dtype=torch.float64, device="cuda")
+    lib.trplk_residual_norms(h, code, n, ld, k, X, AX, None, torch.from_numpy(theta).cuda(), rn, xn)
+    Xg = X.cpu().numpy()[:, :n].T.astype(np.float64)
+    AXg = AX.cpu().numpy()[:, :n].T.astype(np.float64)
+    if prec == "f64":
+        rref, xref = O.residual_norms(AXg, Xg, Xg, theta)
+        assert np.allclose(rn.cpu().numpy(), rref, rtol=1e-13)
+        assert np.allclose(xn.cpu().numpy(), xref, rtol=1e-13)
+    else:
+        th32 = theta.astype(np.float32)
+        R = (AX.cpu().numpy()[:, :n].T - X.cpu().numpy()[:, :n].T * th32[None, :]).astype(np.float64)
+        assert np.allclose(rn.cpu().numpy(), np.linalg.norm(R, axis=0), rtol=1e-6)
+        assert np.allclose(xn.cpu().numpy(), np.linalg.norm(Xg, axis=0), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- start block (bit-exact)
+def test_start_block_bit_exact(lib, h):
+    n, k = 3001, 7
+    ld = ld_of(n)
+    X = torch.zeros((k, ld), dtype=torch.float64, device="cuda")
+    lib.trplk_start_block(h, n, ld, k, 12345, X)
+    ref = W.start_block(n, k, 12345)
+    got = X.cpu().numpy()
+    assert np.array_equal(got[:, :n].T, ref)
+    assert np.all(got[:, n:] == 0)
+
+
+# ---------------------------------------------------------------- a8 final check
+def test_check_residuals_matches_numpy(lib, h):
+    A, B = W.fem_q1_pencil(6)
+    As, Bs = A.to_scipy(), B.to_scipy()
+    p = 4
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((A.n, p))
+    theta = rng.uniform(1, 10, p)
+    ld = ld_of(A.n)
+    out = torch.zeros(p, dtype=torch.float64, device="cuda")
+    nA = O.norm1(As)
+    lib.trplk_check_residuals(h, dev_csr(lib, A), dev_csr(lib, B), ld, p, padded(X, ld),
+                              torch.from_numpy(theta).cuda(), nA, out)
+    ref = np.linalg.norm(As @ X - (Bs @ X) * theta, axis=0) / (nA * np.linalg.norm(X, axis=0))
+    assert np.allclose(out.cpu().numpy(), ref, rtol=1e-13)
+
+
+# ---------------------------------------------------------------- whole solves
+@pytest.mark.parametrize("cycles", [1, 2, 3])
+def test_first_cycles_match_oracle_iterates(lib, h, cycles):
+    """Same start block, same readings: after 1-3 cycles the Ritz values agree
+    to rounding level (the +K block enters from cycle 2 on)."""
+    A = W.diffusion_3d(12, W.lognormal_field(12, 1.0, 21))
+    p, q, k, l = 4, 16, 6, 2
+    X0 = W.start_block(A.n, k, 5)
+    ref = O.solve(A.to_scipy(), None, p, q, k, l, 1e-14, X0, "jacobi", max_cycles=cycles)
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), None, p=p, q=q, k=k, l=l, tol=1e-14, X0=X0,
+                                     max_cycles=cycles)
+    assert info["cycles"] == cycles == ref["cycles"]
+    assert info["mv_A"] == ref["mv_A"]
+    assert np.allclose(ev, ref["evals"], rtol=1e-11)
+    # Ritz vectors: same up to rounding (spectrum is simple here)
+    for i in range(p):
+        c = abs(X[:, i] @ ref["evecs"][:, i])
+        assert c > 1 - 1e-9
+
+
+def test_c1_laplacian_full_size_matches_oracle_and_closed_form(lib, h):
+    """100 x 100 5-point Laplacian, p = 5, q = 20, p_hat = 8, +K = 5, Jacobi, tol 1e-8."""
+    N, p, q, k, l = 100, 5, 20, 8, 5
+    A = W.laplacian_2d(N)
+    X0 = W.start_block(A.n, k, 0)
+    ref = O.solve(A.to_scipy(), None, p, q, k, l, 1e-8, X0, "jacobi")
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), None, p=p, q=q, k=k, l=l, tol=1e-8, X0=X0)
+    assert rc == lib.OK
+    hgrid = math.pi / (2 * (N + 1))
+    lam = np.sort([4 * math.sin(i * hgrid) ** 2 + 4 * math.sin(j * hgrid) ** 2
+                   for i in range(1, 8) for j in range(1, 8)])[:p]
+    assert np.all(np.abs(ev - ref["evals"]) <= 1e-10 * np.abs(ref["evals"]))
+    assert np.all(np.abs(ev - lam) <= 1e-10 * lam)
+    assert np.all(res <= 1e-8)
+    # residuals recomputed by the oracle's matvec
+    As = A.to_scipy()
+    r = np.linalg.norm(As @ X - X * ev, axis=0) / (O.norm1(As) * np.linalg.norm(X, axis=0))
+    assert np.all(r <= 1e-8)
+    assert np.allclose(X.T @ X, np.eye(p), atol=1e-12)
+    assert info["mv_A"] == k + (q - k) * info["cycles"]
+
+
+def test_generalized_fem_pencil_matches_oracle(lib, h):
+    N = 8
+    A, B = W.fem_q1_pencil(N, np.random.default_rng(2).uniform(1, 10, (N, N, N)))
+    As, Bs = A.to_scipy(), B.to_scipy()
+    p, q, k, l = 5, 20, 8, 1
+    X0 = W.start_block(A.n, k, 2)
+    ref = O.solve(As, Bs, p, q, k, l, 1e-9, X0, "jacobi")
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), dev_csr(lib, B), p=p, q=q, k=k, l=l, tol=1e-9, X0=X0)
+    assert rc == lib.OK and ref["status"] == O.OK
+    assert np.all(np.abs(ev - ref["evals"]) <= 1e-10 * np.abs(ref["evals"]))
+    assert np.allclose(X.T @ (Bs @ X), np.eye(p), atol=1e-11)
+    r = np.linalg.norm(As @ X - (Bs @ X) * ev, axis=0) / (O.norm1(As) * np.linalg.norm(X, axis=0))
+    assert np.all(r <= 1e-9)
+    assert info["mv_B"] == info["mv_A"]
+
+
+def test_mixed_precision_matches_oracle(lib, h):
+    N = 20
+    A = W.diffusion_3d(N, W.lognormal_field(N, 1.0, 1))
+    As = A.to_scipy()
+    p, q, k, l = 6, 24, 10, 1
+    X0 = W.start_block(A.n, k, 0)
+    ref = O.solve(As, None, p, q, k, l, 1e-10, X0, "jacobi")
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), None, p=p, q=q, k=k, l=l, tol=1e-10, X0=X0,
+                                     precision=lib.PRECISION_MIXED)
+    assert rc == lib.OK
+    assert np.all(res <= 1e-10)
+    assert np.all(np.abs(ev - ref["evals"]) <= 1e-10 * np.abs(ref["evals"]))
+    assert np.allclose(X.T @ X, np.eye(p), atol=1e-11)
+
+
+def test_ragged_and_degenerate_edges(lib, h):
+    """Tiny n (q = n), p = k = 1, l = 0, no preconditioner."""
+    A = W.laplacian_2d(4)      # n = 16
+    X0 = W.start_block(A.n, 1, 3)
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), None, p=1, q=16, k=1, l=0, tol=1e-10, X0=X0,
+                                     precond=lib.PRECOND_NONE)
+    lam0 = 8 * math.sin(math.pi / 10) ** 2
+    assert rc in (lib.OK, lib.BREAKDOWN)
+    assert abs(ev[0] - lam0) <= 1e-10
+
+
+def test_invalid_arguments_are_rejected(lib, h):
+    A = W.laplacian_2d(10)
+    Ad = dev_csr(lib, A)
+    with pytest.raises(lib.TrplkError) as e:
+        lib.solve(h, Ad, None, p=5, q=8, k=4, l=1)            # k < p
+    assert e.value.code == lib.EINVAL
+    with pytest.raises(lib.TrplkError) as e:
+        lib.solve(h, Ad, None, p=2, q=6, k=4, l=2)            # q < k + l + 1
+    assert e.value.code == lib.EINVAL
+    bad = W.Csr(A.rowptr.copy(), A.col.copy(), A.val.copy())
+    bad.col[5] = A.n + 3                                        # column out of range
+    with pytest.raises(lib.TrplkError) as e:
+        lib.solve(h, dev_csr(lib, bad), None, p=2, q=10, k=4, l=1)
+    assert e.value.code == lib.EINVAL
+    # the handle stays usable afterwards
+    ev, X, res, rc, info = lib.solve(h, Ad, None, p=2, q=12, k=4, l=1, tol=1e-8)
+    assert rc == lib.OK
+
+
+def test_host_inputs_and_outputs(lib, h):
+    """The e2e form: host CSR and host outputs through trplk_solve."""
+    A = W.laplacian_2d(30)
+    hc = lib.make_csr(A.rowptr, A.col, A.val)
+    ev, X, res, rc, info = lib.solve(h, hc, None, p=3, q=14, k=5, l=1, tol=1e-9)
+    assert rc == lib.OK
+    hgrid = math.pi / 62
+    lam = np.sort([4 * math.sin(i * hgrid) ** 2 + 4 * math.sin(j * hgrid) ** 2
+                   for i in range(1, 5) for j in range(1, 5)])[:3]
+    assert np.allclose(ev, lam, rtol=1e-9)
