@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the TRPL+K hot path on one GB300 (or N independent replicas).
+
+Workload: the 3D 7-point variable-coefficient diffusion operator on 128^3
+cells (n = 2,097,152, nnz = 14,581,760, FP64 CSR), coefficients
+lognormal(0, 1) per cell (seed 1); the 10 smallest eigenpairs, Jacobi
+preconditioner, q = 40, p_hat = 15, +K = 1, tol 1e-8 (relative to ||A||_1),
+start block SplitMix64 seed 0.  One step = one whole solve (start block,
+Rayleigh-Ritz, every TRPL+K cycle, FP64 refinement, final FP64 residual
+check).
+
+Reported: seconds per solve of the mixed path (FP32 basis and SpMV,
+FP64-class coefficients, FP64 refinement) with inputs resident in HBM
+(`value`), the plain FP64 path on the same matrix (`fp64_seconds`), the same
+mixed solve end to end from pinned host memory (`e2e`), the roofline of the
+dominant kernel family measured with CUDA events inside the timed region,
+the SpMV bandwidth, and the CPU oracle on a bounded sample (`cpu_baseline`).
+
+`--impl reference` times the CPU oracle (FP64 numpy/scipy) instead.
+Multi-GPU: one process per GPU (torchrun); the path does not shard, so each
+rank runs an independent replica; the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="diffusion3d_128_lognormal", N=128, sigma=1.0, coef_seed=1, p=10, q=40, k=15, l=1, tol=1e-8,
+                seed=0)
+METRIC = "s to p eigpairs @resid 1e-8, learned/FP32 vs plain FP64; SpMV HBM GB/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solves")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def build_workload():
+    from paper_1711_10128_gb300 import workloads as W
+    A = W.diffusion_3d(WORKLOAD["N"], W.lognormal_field(WORKLOAD["N"], WORKLOAD["sigma"], WORKLOAD["coef_seed"]))
+    return A
+
+
+def config_dict(A, path):
+    return {"workload": WORKLOAD["name"], "n": A.n, "nnz": A.nnz, "p": WORKLOAD["p"], "q": WORKLOAD["q"],
+            "k": WORKLOAD["k"], "l": WORKLOAD["l"], "tol": WORKLOAD["tol"], "precond": "jacobi", "path": path,
+            "l2": "inputs larger than L2 (basis 0.3-0.7 GB per copy; matrix 0.17 GB)"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, value, device=None):
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=f"cuda:{device}" if device is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_for(kernel_family):
+    """DRAM traffic per launch of a kernel family from the committed ncu
+    summary, if the kernel sources are unchanged since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    ent = d.get(kernel_family)
+    if not ent:
+        return None
+    h = hashlib.sha256()
+    for f in ent.get("sources", []):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest() != ent.get("sha256"):
+        return None
+    return ent.get("bytes_per_launch_full_size")
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(A):
+    """Time the FP64 oracle on init + 1 and init + 2 cycles of the same solve
+    and extrapolate to a whole solve with the oracle's own cycle count for this
+    workload (stored by oracle/reference_runs.py); returns (seconds, sample text)."""
+    from oracle import trplk as O
+    from paper_1711_10128_gb300 import workloads as W
+    As = A.to_scipy()
+    X0 = W.start_block(A.n, WORKLOAD["k"], WORKLOAD["seed"])
+    args = (As, None, WORKLOAD["p"], WORKLOAD["q"], WORKLOAD["k"], WORKLOAD["l"], WORKLOAD["tol"], X0, "jacobi")
+    t0 = time.perf_counter()
+    O.solve(*args, max_cycles=1)
+    t1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.solve(*args, max_cycles=2)
+    t2 = time.perf_counter() - t0
+    per_cycle = max(t2 - t1, 1e-9)
+    init = max(t1 - per_cycle, 0.0)
+    ref = os.path.join(ROOT, "oracle", "reference_runs.json")
+    cycles, src = None, None
+    if os.path.exists(ref):
+        d = json.load(open(ref)).get("diffusion128")
+        if d:
+            cycles, src = d["cycles"], "oracle full run"
+    if cycles is None:
+        cycles, src = 125, "cycle count of the FP64 GPU solve"
+    secs = init + per_cycle * cycles
+    text = (f"oracle init + 1 and + 2 cycles timed ({t1:.1f} s, {t2:.1f} s): init {init:.1f} s, "
+            f"{per_cycle:.1f} s/cycle, extrapolated to {cycles} cycles ({src})")
+    return secs, text
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return 0
+    A = build_workload()
+    vals = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        secs, sample = oracle_sample(A) if i >= args.warmup or i == 0 else (None, sample)
+        if i >= args.warmup:
+            vals.append(secs)
+    value = statistics.mean(vals)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(A, "cpu oracle fp64"),
+            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our path
+def run_ours(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1711_10128_gb300 import binding as lib
+
+    A = build_workload()
+    dev = f"cuda:{local}"
+    stream = torch.cuda.Stream(device=dev)
+    h = lib.Handle(local, stream.cuda_stream)
+    rp, cl, vl = (torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.col).to(dev),
+                  torch.from_numpy(A.val).to(dev))
+    Ad = lib.make_csr(rp, cl, vl)
+    P = WORKLOAD
+    n, p = A.n, P["p"]
+    ev_d = torch.zeros(p, dtype=torch.float64, device=dev)
+    X_d = torch.zeros((p, n), dtype=torch.float64, device=dev)
+    r_d = torch.zeros(p, dtype=torch.float64, device=dev)
+
+    def solve_device(precision):
+        info = lib.trplk_info()
+        params = lib.make_params(P["p"], P["q"], P["k"], P["l"], P["tol"], 5000, P["seed"], lib.PRECOND_JACOBI,
+                                 precision, 1)
+        rc = lib.trplk_solve(h, Ad, None, params, None, ev_d, X_d, r_d, info)
+        return rc, info.as_dict()
+
+    def timed(precision, steps, warmup, profile=False):
+        for _ in range(warmup):
+            solve_device(precision)
+        torch.cuda.synchronize(dev)
+        barrier(pg, local)
+        sampler = ClockSampler(local)
+        sampler.start()
+        if profile:
+            lib.trplk_profile(h, 1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        infos = []
+        e0.record(stream)
+        for _ in range(steps):
+            rc, info = solve_device(precision)
+            if rc != lib.OK:
+                raise RuntimeError(f"solve did not converge: {info}")
+            infos.append(info)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = lib.profile_summary(h) if profile else {}
+        if profile:
+            lib.trplk_profile(h, 0)
+        clocks = sampler.stop()
+        torch.cuda.synchronize(dev)
+        barrier(pg, local)
+        return ms, infos, prof, clocks
+
+    # headline: mixed path, inputs resident in HBM
+    ms_mixed, infos, prof, clocks = timed(lib.PRECISION_MIXED, args.steps, args.warmup, profile=True)
+    ms_mixed = max_over_ranks(pg, ms_mixed, local)
+    out = {"metric": METRIC, "value": ms_mixed / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config_dict(A, "mixed")}
+    info = infos[-1]
+    out["solve"] = {k: info[k] for k in ("cycles", "refine_cycles", "mv_A", "prec_apply", "nconv", "max_resid")}
+    out["gpu_launches"] = int(sum(i["launches"] for i in infos))
+    out["clocks"] = clocks
+    if world > 1:
+        out["solves_per_s"] = world * 1e3 / ms_mixed
+
+    # roofline of the dominant HBM-streaming kernel family (CUDA events, timed region)
+    hbm_peak, peak_src = measured_peaks()
+    fam = {k: v for k, v in prof.items() if v[2] > 0}
+    if fam:
+        dom = max(fam, key=lambda k: fam[k][1])
+        nl, tms, by = fam[dom]
+        achieved = by / (tms / 1e3) / 1e9
+        out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": achieved / hbm_peak, "peak_source": peak_src, "traffic": traffic_for(dom),
+                           "launches": nl, "avg_launch_us": tms * 1e3 / nl,
+                           "algorithmic_bytes_per_launch": by / nl}
+    tot = sum(v[1] for v in prof.values()) or 1.0
+    out["kernel_time_share"] = {k: round(v[1] / tot, 4) for k, v in sorted(prof.items(), key=lambda x: -x[1][1])}
+    for key in ("spmv_scaled", "spmv"):
+        if key in prof and prof[key][1] > 0:
+            nl, tms, by = prof[key]
+            out["spmv_gbs"] = by / (tms / 1e3) / 1e9
+            break
+
+    # comparison: plain FP64 path on the same matrix
+    if not args.no_fp64:
+        ms64, infos64, _, _ = timed(lib.PRECISION_FP64, max(1, args.steps), 1)
+        ms64 = max_over_ranks(pg, ms64, local)
+        out["fp64_seconds"] = ms64 / 1e3
+        out["fp64_cycles"] = infos64[-1]["cycles"]
+        out["speedup_vs_fp64"] = ms64 / ms_mixed
+
+    # end to end: host CSR in pinned memory, host outputs
+    if not args.no_e2e:
+        rp_h = torch.from_numpy(A.rowptr).pin_memory()
+        cl_h = torch.from_numpy(A.col).pin_memory()
+        vl_h = torch.from_numpy(A.val).pin_memory()
+        Ah = lib.make_csr(rp_h.numpy(), cl_h.numpy(), vl_h.numpy())
+        ev_h = torch.zeros(p, dtype=torch.float64).pin_memory()
+        X_h = torch.zeros((p, n), dtype=torch.float64).pin_memory()
+        r_h = torch.zeros(p, dtype=torch.float64).pin_memory()
+        params = lib.make_params(P["p"], P["q"], P["k"], P["l"], P["tol"], 5000, P["seed"], lib.PRECOND_JACOBI,
+                                 lib.PRECISION_MIXED, 0)
+        ts = []
+        for i in range(1 + args.steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            lib.trplk_solve(h, Ah, None, params, None, ev_h, X_h, r_h, lib.trplk_info())
+            if i >= 1:
+                ts.append(time.perf_counter() - t0)
+        e2e = max_over_ranks(pg, statistics.mean(ts), local)
+        h2d = A.rowptr.nbytes + A.col.nbytes + A.val.nbytes
+        d2h = ev_h.numel() * 8 + X_h.numel() * 8 + r_h.numel() * 8
+        out["e2e"] = {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # CPU oracle on a bounded sample (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, sample = oracle_sample(A)
+        out["cpu_baseline"] = {"value": secs, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": sample}
+    h.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank, pg)
+        return run_ours(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -94,7 +94,10 @@ typedef struct {
  *  outputs_on_device  1: evals/evecs/resid are device pointers; 0: host
  *  fsai_*     the sparse lower-triangular factor G (CSR, F64 values, same
  *             on_device as A) when precond = TRPLK_PRECOND_FSAI; M = G^T G
- *  mixed_tol  FP32-phase tolerance of the mixed path (0 = 1e-6)          */
+ *  mixed_tol  FP32-phase tolerance of the mixed path (0 = max(tol, 3e-8));
+ *             the FP32 phase also stops when the target's relative residual,
+ *             once below 1e-6, has not halved over 30 cycles; FP64 cycles
+ *             then finish to tol                                         */
 typedef struct {
   int p, q, k, l;
   double tol;
@@ -119,6 +122,7 @@ typedef struct {
   int nconv;              /* pairs meeting tol in the final check             */
   double normA;           /* ||A||_1                                          */
   double max_resid;       /* largest final relative residual                  */
+  int64_t launches;       /* kernel launches of this call                     */
 } trplk_info;
 
 /* Create a handle bound to CUDA device `device`.  cuda_stream: a
@@ -220,6 +224,26 @@ trplk_status trplk_start_block(trplk_handle* h, int64_t n, int64_t ld, int k, ui
 trplk_status trplk_check_residuals(trplk_handle* h, const trplk_csr* A, const trplk_csr* B,
                                    int64_t ld, int p, const double* X, const double* theta,
                                    double normA, double* resid);
+
+/* ------------------------------------------------------------------------
+ * Per-kernel profiling (measurement support, not part of the method).
+ * ---------------------------------------------------------------------- */
+
+/* enable = 1: from now on bracket every kernel launch of this handle with
+ * CUDA events on its stream and record the launch's algorithmic bytes
+ * (every operand read once, every output written once); enable = 0: stop.
+ * Either call clears what was recorded. */
+trplk_status trplk_profile(trplk_handle* h, int enable);
+
+/* Totals since the last trplk_profile(h, 1) for one kernel family `kind`
+ * (0 <= kind < 12; see trplk_profile_kind_name): number of launches, summed
+ * event time in milliseconds and summed algorithmic bytes.  EINVAL for a
+ * bad kind or NULL output. */
+trplk_status trplk_profile_read(trplk_handle* h, int kind, int64_t* launches, double* milliseconds,
+                                double* bytes);
+
+/* Name of kernel family `kind`, or NULL if out of range.  Static storage. */
+const char* trplk_profile_kind_name(int kind);
 
 #ifdef __cplusplus
 }

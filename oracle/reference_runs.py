@@ -1,0 +1,60 @@
+"""Run the oracle to convergence on the full-size workloads and store the
+results in oracle/reference_runs.json -- TEST INFRASTRUCTURE ONLY.
+
+The stored eigenvalues are the FP64 oracle's answer for the full-size
+operators (used as full-size parity references), and the stored cycle counts
+and per-phase timings let the CPU-baseline measurement extrapolate a bounded
+sample of the oracle to a whole solve.  Calls only ``oracle/`` and the seeded
+input generators.  Usage: python -m oracle.reference_runs [name ...]
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+from oracle import trplk as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "reference_runs.json")
+
+
+def workloads():
+    from paper_1711_10128_gb300 import workloads as W
+    return {
+        # 3D 7-point lognormal(0,1) diffusion on 128^3, 10 smallest, Jacobi, q=40, p_hat=15, +K=1, tol 1e-8
+        "diffusion128": dict(build=lambda: (W.diffusion_3d(128, W.lognormal_field(128, 1.0, 1)), None),
+                             p=10, q=40, k=15, l=1, tol=1e-8, seed=0),
+        # 2D 5-point Laplacian on 100x100, 5 smallest, Jacobi, q=20, p_hat=8, +K=5, tol 1e-8
+        "laplace100": dict(build=lambda: (W.laplacian_2d(100), None), p=5, q=20, k=8, l=5, tol=1e-8, seed=0),
+    }
+
+
+def run(name):
+    from paper_1711_10128_gb300 import workloads as W
+    cfg = workloads()[name]
+    A, B = cfg["build"]()
+    As = A.to_scipy()
+    X0 = W.start_block(A.n, cfg["k"], cfg["seed"])
+    t0 = time.perf_counter()
+    r = O.solve(As, None if B is None else B.to_scipy(), cfg["p"], cfg["q"], cfg["k"], cfg["l"], cfg["tol"], X0,
+                "jacobi")
+    secs = time.perf_counter() - t0
+    return dict(n=A.n, nnz=A.nnz, p=cfg["p"], q=cfg["q"], k=cfg["k"], l=cfg["l"], tol=cfg["tol"],
+                status=r["status"], cycles=r["cycles"], mv_A=r["mv_A"], evals=[float(x) for x in r["evals"]],
+                resid=[float(x) for x in r["resid"]], seconds=secs, cores=os.cpu_count())
+
+
+def main(names):
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for name in names:
+        data[name] = run(name)
+        json.dump(data, open(OUT, "w"), indent=1)
+        print(name, data[name]["status"], data[name]["cycles"], data[name]["seconds"], flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or ["laplace100", "diffusion128"])

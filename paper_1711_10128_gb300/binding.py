@@ -41,7 +41,7 @@ class trplk_params(C.Structure):
 class trplk_info(C.Structure):
     _fields_ = [("cycles", C.c_int), ("refine_cycles", C.c_int), ("mv_A", C.c_int64), ("mv_B", C.c_int64),
                 ("prec_apply", C.c_int64), ("mv_check", C.c_int64), ("seconds", C.c_double),
-                ("nconv", C.c_int), ("normA", C.c_double), ("max_resid", C.c_double)]
+                ("nconv", C.c_int), ("normA", C.c_double), ("max_resid", C.c_double), ("launches", C.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -74,6 +74,9 @@ def _load():
         "trplk_residual_norms": (st, [vp, i32, i64, i64, i32, vp, vp, vp, vp, vp, vp]),
         "trplk_start_block": (st, [vp, i64, i64, i32, C.c_uint64, vp]),
         "trplk_check_residuals": (st, [vp, C.POINTER(trplk_csr), C.POINTER(trplk_csr), i64, i32, vp, vp, dbl, vp]),
+        "trplk_profile": (st, [vp, i32]),
+        "trplk_profile_read": (st, [vp, i32, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "trplk_profile_kind_name": (C.c_char_p, [i32]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -207,6 +210,37 @@ def trplk_start_block(h, n, ld, k, seed, X):
 def trplk_check_residuals(h, A, B, ld, p, X, theta, normA, resid):
     return h.check(LIB.trplk_check_residuals(h.h, C.byref(A), C.byref(B) if B is not None else None, ld, p, ptr(X),
                                              ptr(theta), float(normA), ptr(resid)))
+
+
+def trplk_profile(h, enable):
+    return h.check(LIB.trplk_profile(h.h, int(enable)))
+
+
+def trplk_profile_read(h, kind):
+    """(launches, milliseconds, algorithmic bytes) of one kernel family."""
+    n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+    h.check(LIB.trplk_profile_read(h.h, kind, C.byref(n), C.byref(ms), C.byref(by)))
+    return n.value, ms.value, by.value
+
+
+def trplk_profile_kind_name(kind):
+    r = LIB.trplk_profile_kind_name(kind)
+    return r.decode() if r else None
+
+
+def profile_summary(h):
+    """{family name: (launches, ms, bytes)} for every family with launches."""
+    out = {}
+    k = 0
+    while True:
+        name = trplk_profile_kind_name(k)
+        if name is None:
+            break
+        n, ms, by = trplk_profile_read(h, k)
+        if n:
+            out[name] = (n, ms, by)
+        k += 1
+    return out
 
 
 # ---------------------------------------------------------------- convenience

@@ -1,8 +1,46 @@
 // Host-side launch wrappers shared by the translation units of libtrplk.
 #pragma once
+#include <vector>
+
 #include "common.cuh"
 
 namespace trplk {
+
+// Kernel families timed by the optional per-launch profiler.
+enum ProfKind : int {
+  PK_SPMV = 0, PK_SPMV_SCALED, PK_TS_PROJ, PK_TS_INNER, PK_TS_UPDPROJ, PK_TS_UPDNORM, PK_TS_UPD,
+  PK_TS_ROT, PK_TS_RESID, PK_TS_DOT, PK_RR, PK_OTHER, PK_COUNT
+};
+
+// Counts every kernel launch; when `on`, brackets each launch with CUDA
+// events on the launching stream and records its algorithmic bytes.
+struct Profiler {
+  bool on = false;
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  struct Rec {
+    int kind;
+    size_t e0, e1;
+    double bytes;
+  };
+  std::vector<Rec> recs;
+  size_t take() {
+    if (next == pool.size()) {
+      cudaEvent_t e;
+      TRPLK_CUDA_TRY(cudaEventCreate(&e));
+      pool.push_back(e);
+    }
+    return next++;
+  }
+  void reset() {
+    next = 0;
+    recs.clear();
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
 
 // Per-handle device context: stream, SM count and the small scratch every
 // reduction kernel shares (kernels on one stream run one after another).
@@ -13,6 +51,32 @@ struct Ctx {
   double* partials = nullptr;      // [kMaxPartials][kPartialStride]
   unsigned int* counter = nullptr; // last-CTA ticket, kept at zero between kernels
   int* status = nullptr;           // device status word (kFlag*)
+  Profiler* prof = nullptr;
+};
+
+// RAII bracket of one kernel launch for the profiler.
+struct ProfScope {
+  const Ctx& c;
+  int kind;
+  double bytes;
+  size_t e0 = (size_t)-1;
+  ProfScope(const Ctx& c_, int kind_, double bytes_) : c(c_), kind(kind_), bytes(bytes_) {
+    if (!c.prof) return;
+    c.prof->launches++;
+    if (c.prof->on) {
+      e0 = c.prof->take();
+      TRPLK_CUDA_TRY(cudaEventRecord(c.prof->pool[e0], c.stream));
+    }
+  }
+  ~ProfScope() {
+    if (!c.prof || e0 == (size_t)-1) return;
+    try {
+      size_t e1 = c.prof->take();
+      if (cudaEventRecord(c.prof->pool[e1], c.stream) == cudaSuccess) c.prof->recs.push_back({kind, e0, e1, bytes});
+    } catch (...) {
+      // a failed event never hides the error of the launch itself
+    }
+  }
 };
 constexpr int kPartialStride = 2 * kMaxQ;
 

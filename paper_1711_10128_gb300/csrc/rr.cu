@@ -187,6 +187,7 @@ void rayleigh_ritz(const Ctx& c, int w, const double* T, int ldT, double* theta,
                                         2 * kMaxQ * (kMaxQ + 1) * (int)sizeof(double)));
     cfg = true;
   }
+  ProfScope ps(c, PK_RR, 0.0);
   rr_jacobi_kernel<<<1, kThreads, smem, c.stream>>>(w, T, ldT, theta, Y, c.status);
   check_launch("rr_jacobi_kernel");
 }

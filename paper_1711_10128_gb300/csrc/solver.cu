@@ -23,6 +23,7 @@ using namespace trplk;
 // ---------------------------------------------------------------- handle
 struct trplk_handle {
   Ctx ctx;
+  Profiler prof;
   bool own_stream = false;
   std::string err;
   struct Buf {
@@ -175,11 +176,13 @@ Operator make_operator(trplk_handle* h, const trplk_csr* M, const std::string& t
   op.d.nnz = op.nnz;
   // structural validation on the device (column range, monotone rows)
   h->clear_status();
+  ProfScope ps1(c, PK_OTHER, 0.0);
   validate_csr_kernel<<<std::max(1, std::min<int>((int)((op.n + 255) / 256), c.sms * 8)), 256, 0, c.stream>>>(
       op.n, op.nnz, op.d.rowptr, op.d.col, c.status);
   check_launch("validate_csr");
   const int nb = std::max(1, std::min<int>((int)((op.n + 255) / 256), 1024));
   auto* part = static_cast<double*>(h->get("norm1.part", 1024 * sizeof(double)));
+  ProfScope ps2(c, PK_OTHER, 0.0);
   row_abs_sum_kernel<double><<<nb, 256, 0, c.stream>>>(op.n, op.d.rowptr, op.d.val, part);
   check_launch("row_abs_sum");
   double* hp = h->host(1024);
@@ -220,6 +223,10 @@ struct Solver {
   int max_cycles;
   bool hasB;
   bool skip_converged;          // refinement phase: targets skip converged pairs
+  bool check_start = false;     // replace dependent start columns (refinement phase)
+  int stall_window = 0;         // >0: stop when the target residual stagnates
+  bool stalled = false;
+  double* tmp64 = nullptr;
   const Operator& Aop;
   const Operator& Bop;
   const DevCsr<S>& A;
@@ -266,6 +273,7 @@ struct Solver {
     betas = static_cast<double*>(h->get(tag + ".betas", 2 * (kMaxQ + 8) * sizeof(double)));
     scale = static_cast<double*>(h->get(tag + ".scale", 8 * sizeof(double)));
     rn = static_cast<double*>(h->get(tag + ".rn", kMaxQ * sizeof(double)));
+    tmp64 = static_cast<double*>(h->get(tag + ".tmp64", ld * sizeof(double), fresh));
     xn = static_cast<double*>(h->get(tag + ".xn", kMaxQ * sizeof(double)));
   }
 
@@ -331,11 +339,24 @@ struct Solver {
     } else {
       convert<S, double>(c, (int64_t)ld * k, X0, U[0]);
     }
-    // B-orthonormalise column by column (CGS2) and form A X (Algorithm 1 input)
+    // B-orthonormalise column by column (CGS2) and form A X (Algorithm 1 input).
+    // A column that is (numerically) in the span of the previous ones is
+    // replaced by a fresh SplitMix64 column once; the replacement matters when
+    // the start block comes from a lower-precision phase.
     for (int j = 0; j < k; ++j) {
-      TRPLK_CUDA_TRY(cudaMemcpyAsync(v, col(U[0], j), ld * sizeof(S), cudaMemcpyDeviceToDevice, c.stream));
-      ts_project<S>(c, ld, j, BU[0], v, h1);
-      orthonormalize_tail(0, j, j, out);
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        TRPLK_CUDA_TRY(cudaMemcpyAsync(v, col(U[0], j), ld * sizeof(S), cudaMemcpyDeviceToDevice, c.stream));
+        ts_project<S>(c, ld, j, BU[0], v, h1);
+        orthonormalize_tail(0, j, j, out);
+        if (!check_start) break;
+        double* hb = h->host(2);
+        TRPLK_CUDA_TRY(cudaMemcpyAsync(hb, betas + 2 * j, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        h->sync();
+        if (hb[0] > eps_breakdown * hb[1]) break;
+        if (attempt == 1) throw Error(TRPLK_EINVAL, "start block is numerically rank deficient");
+        start_block(c, n, ld, 1, 0x5DEECE66Dull ^ (uint64_t)(j + 1) * 0x9E3779B97F4A7C15ull, tmp64);
+        convert<S, double>(c, ld, tmp64, col(U[0], j));
+      }
       append(0, j, out);
     }
     // T = X^T A X (upper triangle), initial RR
@@ -344,9 +365,10 @@ struct Solver {
     std::vector<double> th, r, x, bet;
     read_back(k, th, r, x, &bet, k);
     check_flags(h, kFlagBreakdown);
-    for (int j = 0; j < k; ++j)
-      if (!(bet[2 * j] > eps_breakdown * bet[2 * j + 1]))
-        throw Error(TRPLK_EINVAL, "start block is numerically rank deficient");
+    if (!check_start)
+      for (int j = 0; j < k; ++j)
+        if (!(bet[2 * j] > eps_breakdown * bet[2 * j + 1]))
+          throw Error(TRPLK_EINVAL, "start block is numerically rank deficient");
 
     auto converged_vec = [&](const std::vector<double>& rr, const std::vector<double>& xx) {
       std::vector<char> cv(k);
@@ -366,12 +388,17 @@ struct Solver {
     }
     // X_prev: columns [xp_start, xp_start + xp_count) of U[xp_buf]
     int xp_buf = -1, xp_start = 0, xp_count = 0;
+    std::vector<double> hist;   // stagnation detection
+    int hist_t = -1;
 
     for (int cycle = 1; cycle <= max_cycles; ++cycle) {
       out.cycles = cycle;
       const double rho = th[t];
       h->clear_status();
-      set_diag_block_kernel<<<1, 256, 0, c.stream>>>(T, ldT, k, theta);
+      {
+        ProfScope ps(c, PK_OTHER, 0.0);
+        set_diag_block_kernel<<<1, 256, 0, c.stream>>>(T, ldT, k, theta);
+      }
       check_launch("set_diag_block");
       // first Lanczos vector u = M (A x_t - rho B x_t)  (Algorithm 1, restart)
       restart_vector<S>(c, ld, col(AU[cur], t), col(BU[cur], t), theta + t, dinv, pmode, v);
@@ -433,6 +460,23 @@ struct Solver {
       read_back(k, th, r, x, nullptr, 0);
       check_flags(h, kFlagBreakdown);
       auto cv = converged_vec(r, x);
+      if (stall_window > 0) {
+        // the target's relative residual, tracked while the target is unchanged
+        const double rel = r[t] / (normA * x[t]);
+        if (hist_t != t) {
+          hist.clear();
+          hist_t = t;
+        }
+        hist.push_back(rel);
+        // only below 1e-6, where FP32 rounding can hold a residual up
+        if (!cv[t] && rel < 1e-6 && (int)hist.size() > stall_window &&
+            rel > 0.5 * hist[hist.size() - 1 - stall_window]) {
+          stalled = true;
+          out.theta = th;
+          out.cur = cur;
+          return out;
+        }
+      }
       xp_buf = old;
       xp_start = nxt_start;
       xp_count = nxt_count;
@@ -541,6 +585,7 @@ trplk_status trplk_create(trplk_handle** out, int device, void* stream) {
   auto* h = new trplk_handle();
   try {
     h->ctx.device = device;
+    h->ctx.prof = &h->prof;
     TRPLK_CUDA_TRY(cudaSetDevice(device));
     TRPLK_CUDA_TRY(cudaDeviceGetAttribute(&h->ctx.sms, cudaDevAttrMultiProcessorCount, device));
     if (stream) {
@@ -579,6 +624,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
                          const double* X0, double* evals, double* evecs, double* resid, trplk_info* info) {
   return guarded(h, [&]() -> trplk_status {
     auto t0 = std::chrono::steady_clock::now();
+    const int64_t launches0 = h->prof.launches;
     if (!A) throw Error(TRPLK_EINVAL, "A is NULL");
     if (!evals || !evecs || !resid) throw Error(TRPLK_EINVAL, "output pointer is NULL");
     validate_params(P, A->n);
@@ -627,9 +673,13 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
       theta_dev = S.theta;
       breakdown = res.breakdown && !res.converged;
     } else {
-      const double tol32 = P->mixed_tol > 0.0 ? P->mixed_tol : 1e-6;
+      // FP32 phase: to mixed_tol, by default max(tol, 3e-8) -- about half the
+      // FP32 unit roundoff, the level at which Ritz vectors stored in FP32 stop
+      // improving; a target stuck below 1e-6 for 30 cycles also ends the phase
+      const double tol32 = P->mixed_tol > 0.0 ? P->mixed_tol : std::max(P->tol, 3e-8);
       Solver<float> S32(h, "f32", n, P->p, P->q, P->k, P->l, std::max(tol32, P->tol), P->max_cycles, Aop, Bop, hasB,
                         dinv32, pmode);
+      S32.stall_window = 30;
       SolveOut r32 = S32.run(X0d);
       // promote the k Ritz vectors and refine in FP64 from them
       double* Xr = static_cast<double*>(h->get("Xrefine", (size_t)ld * P->k * sizeof(double)));
@@ -637,6 +687,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
       Solver<double> S64(h, "f64", n, P->p, P->q, P->k, P->l, P->tol, std::max(1, P->max_cycles - r32.cycles), Aop,
                          Bop, hasB, dinv64, pmode);
       S64.skip_converged = true;
+      S64.check_start = true;
       SolveOut r64 = S64.run(Xr);
       inf.cycles = r32.cycles;
       inf.refine_cycles = r64.cycles;
@@ -670,6 +721,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
     }
     h->sync();
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    inf.launches = h->prof.launches - launches0;
     if (info) *info = inf;
     if (inf.nconv == P->p) return TRPLK_OK;
     if (breakdown) {
@@ -828,6 +880,46 @@ trplk_status trplk_check_residuals(trplk_handle* h, const trplk_csr* A, const tr
     check_residuals_fp64(h, Aop, B ? &Bop : nullptr, ld, p, X, theta, normA, rh.data());
     TRPLK_CUDA_TRY(cudaMemcpy(resid, rh.data(), p * sizeof(double), cudaMemcpyHostToDevice));
     check_flags(h, 0);
+    return TRPLK_OK;
+  });
+}
+
+static const char* kProfNames[PK_COUNT] = {"spmv", "spmv_scaled", "ts_project", "ts_inner", "ts_update_project",
+                                           "ts_update_norm", "ts_update", "ts_rotate", "ts_resid", "ts_dot",
+                                           "rayleigh_ritz", "other"};
+
+trplk_status trplk_profile(trplk_handle* h, int enable) {
+  return guarded(h, [&]() -> trplk_status {
+    h->sync();
+    h->prof.reset();
+    h->prof.on = enable != 0;
+    return TRPLK_OK;
+  });
+}
+
+const char* trplk_profile_kind_name(int kind) {
+  return (kind >= 0 && kind < PK_COUNT) ? kProfNames[kind] : nullptr;
+}
+
+trplk_status trplk_profile_read(trplk_handle* h, int kind, int64_t* launches, double* milliseconds,
+                                double* bytes) {
+  return guarded(h, [&]() -> trplk_status {
+    if (kind < 0 || kind >= PK_COUNT || !launches || !milliseconds || !bytes)
+      throw Error(TRPLK_EINVAL, "bad profile query");
+    h->sync();
+    int64_t n = 0;
+    double ms = 0.0, by = 0.0;
+    for (const auto& r : h->prof.recs) {
+      if (r.kind != kind) continue;
+      float t = 0.f;
+      TRPLK_CUDA_TRY(cudaEventElapsedTime(&t, h->prof.pool[r.e0], h->prof.pool[r.e1]));
+      ++n;
+      ms += t;
+      by += r.bytes;
+    }
+    *launches = n;
+    *milliseconds = ms;
+    *bytes = by;
     return TRPLK_OK;
   });
 }

@@ -39,17 +39,42 @@ __global__ void __launch_bounds__(kRows) spmv_kernel(int64_t n, const int64_t* _
   const int64_t end = rowptr[r1];
   const int64_t my_s = row < n ? rowptr[row] : end;
   const int64_t my_e = row < n ? rowptr[row + 1] : end;
+  constexpr int PER = CH / kRows;   // elements each thread stages per chunk
   S sum = 0;
   for (int64_t c0 = base; c0 < end; c0 += CH) {
-    const int64_t c1 = c0 + CH < end ? c0 + CH : end;
-    for (int64_t e = c0 + threadIdx.x; e < c1; e += kRows) {
-      s_val[e - c0] = val[e];
-      s_col[e - c0] = col[e];
+    const int cnt = (int)(end - c0 < CH ? end - c0 : CH);
+    // issue every load of the chunk before the first shared-memory store
+    S vv[PER];
+    int32_t cc[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + u * kRows;
+      if (e < cnt) {
+        vv[u] = val[c0 + e];
+        cc[u] = col[c0 + e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + u * kRows;
+      if (e < cnt) {
+        s_val[e] = vv[u];
+        s_col[e] = cc[u];
+      }
     }
     __syncthreads();
-    const int64_t lo = my_s > c0 ? my_s : c0;
-    const int64_t hi = my_e < c1 ? my_e : c1;
-    for (int64_t e = lo; e < hi; ++e) sum = fmaS(s_val[e - c0], __ldg(&x[s_col[e - c0]]), sum);
+    const int lo = (int)((my_s > c0 ? my_s : c0) - c0);
+    const int hi = (int)((my_e < c0 + cnt ? my_e : c0 + cnt) - c0);
+    int e = lo;
+    for (; e + 4 <= hi; e += 4) {   // four independent gathers in flight
+      const S x0 = __ldg(&x[s_col[e]]), x1 = __ldg(&x[s_col[e + 1]]);
+      const S x2 = __ldg(&x[s_col[e + 2]]), x3 = __ldg(&x[s_col[e + 3]]);
+      sum = fmaS(s_val[e], x0, sum);
+      sum = fmaS(s_val[e + 1], x1, sum);
+      sum = fmaS(s_val[e + 2], x2, sum);
+      sum = fmaS(s_val[e + 3], x3, sum);
+    }
+    for (; e < hi; ++e) sum = fmaS(s_val[e], __ldg(&x[s_col[e]]), sum);
     __syncthreads();
   }
   if (row < n) {
@@ -72,6 +97,11 @@ void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const doubl
   const size_t smem = CH * (sizeof(S) + sizeof(int32_t));
   const int64_t blocks = (A.n + kRows - 1) / kRows;
   if (blocks > 0x7fffffff) throw Error(TRPLK_EINVAL, "matrix too large");
+  // algorithmic bytes: values + column indices + row pointers, x once, y (and
+  // the scaled copies) written once
+  double bytes = (double)A.nnz * (sizeof(S) + 4) + (double)(A.n + 1) * 8 + 2.0 * A.n * sizeof(S);
+  if (scaled) bytes += (double)A.n * sizeof(S) * (bx ? 3 : 1);
+  ProfScope ps(c, scaled ? PK_SPMV_SCALED : PK_SPMV, bytes);
   if (scaled) {
     static bool cfg = false;
     if (!cfg) { TRPLK_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); cfg = true; }
@@ -167,6 +197,7 @@ void spmv_scaled(const Ctx& c, const DevCsr<S>& A, const S* x, const double* sca
 template <typename S>
 void restart_vector(const Ctx& c, int64_t ld, const S* ax, const S* bx, const double* theta_t,
                     const S* dinv, int pmode, S* v) {
+  ProfScope ps(c, PK_OTHER, 0.0);
   restart_vector_kernel<S><<<grid_for(c, ld), 256, 0, c.stream>>>(ld, ax, bx, theta_t, dinv, pmode, v);
   check_launch("restart_vector");
 }
@@ -174,23 +205,27 @@ void restart_vector(const Ctx& c, int64_t ld, const S* ax, const S* bx, const do
 template <typename D, typename S>
 void convert(const Ctx& c, int64_t count, const S* src, D* dst) {
   if (count == 0) return;
+  ProfScope ps(c, PK_OTHER, 0.0);
   convert_kernel<D, S><<<grid_for(c, count), 256, 0, c.stream>>>(count, src, dst);
   check_launch("convert");
 }
 
 void start_block(const Ctx& c, int64_t n, int64_t ld, int k, uint64_t seed, double* X) {
+  ProfScope ps(c, PK_OTHER, 0.0);
   start_block_kernel<<<grid_for(c, ld * k), 256, 0, c.stream>>>(n, ld, k, seed, X);
   check_launch("start_block");
 }
 
 template <typename S>
 void jacobi_dinv(const Ctx& c, const DevCsr<S>& A, S* dinv) {
+  ProfScope ps(c, PK_OTHER, 0.0);
   jacobi_dinv_kernel<S><<<grid_for(c, A.n), 256, 0, c.stream>>>(A.n, A.rowptr, A.col, A.val, dinv, c.status);
   check_launch("jacobi_dinv");
 }
 
 template <typename S>
 void axpby_shift(const Ctx& c, int64_t ld, const S* x, const S* y, double rho, S* r) {
+  ProfScope ps(c, PK_OTHER, 0.0);
   axpby_shift_kernel<S><<<grid_for(c, ld), 256, 0, c.stream>>>(ld, x, y, rho, r);
   check_launch("axpby_shift");
 }

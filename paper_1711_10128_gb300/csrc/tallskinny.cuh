@@ -3,17 +3,23 @@
 // Every pass of the inner step, the +K block and the restart streams U (and
 // A U or B U) from HBM once.  The kernels share one engine:
 //  * persistent CTAs, grid = SMs x CTAs-per-SM (never more than the tiles);
-//  * a CTA has TR threads and walks TR-row tiles with stride gridDim.x;
-//  * one warp stages each tile into shared memory with 1D bulk copies (the
-//    TMA engine, cp.async.bulk): one 1 KiB copy per column segment and per
-//    vector segment, completion counted on an mbarrier; up to 4 stages are in
-//    flight so HBM latency is hidden behind the compute of earlier tiles;
+//    a CTA walks TR-row tiles with stride gridDim.x;
+//  * warp specialisation: one producer warp stages each tile into shared
+//    memory with 1D bulk copies (the TMA engine, cp.async.bulk) -- one 1 KiB
+//    copy per column segment and per vector segment -- and NW = TR/32
+//    consumer warps compute on it; every stage has a "full" mbarrier
+//    (transaction bytes) and an "empty" mbarrier (one arrival per consumer
+//    warp), so consumers run ahead by up to STAGES tiles and the producer
+//    refills a stage as soon as the last consumer has left it;
 //  * compute reads shared memory only: thread-per-row for the updates
-//    v <- v - U h, column-per-warp for the projections U^T v;
+//    v <- v - U h, and balanced (column, row-slice) tasks for the projections
+//    U^T v, each task with its own accumulator;
 //  * projections accumulate in FP64 (double data) or Dot2-compensated FP32
 //    (float data), are reduced per CTA and then summed in CTA order by the
 //    last CTA to finish (deterministic, no floating-point atomics).
 // Rows n..ld-1 of every array are zero, so whole tiles are always copied.
+// Every wait is bounded: a stage that never arrives sets kFlagTimeout, the
+// kernel drains the copies it issued and returns.
 #pragma once
 #include "common.cuh"
 
@@ -67,15 +73,45 @@ struct TSArgs {
   int* status;           // device status word (flags)
 };
 
+// Row slices per tile for the projection tasks: a task is (column, slice)
+// and a lane covers RPS = TR / (32 NQ) rows of its slice.
+template <typename S> struct Slices;
+template <> struct Slices<double> { static constexpr int NQ = 1; };
+template <> struct Slices<float> { static constexpr int NQ = 2; };
+
 template <typename S>
-__device__ __forceinline__ void ts_issue_tile(const TSArgs<S>& a, unsigned char* stage, uint64_t* bar,
-                                              int tile) {
-  constexpr int TR = Tile<S>::TR;
-  constexpr uint32_t colbytes = TR * sizeof(S);
-  const int lane = threadIdx.x & 31;
+struct TSLayout {
+  static constexpr int TR = Tile<S>::TR;
+  static constexpr int NW = TR / 32;              // consumer warps
+  static constexpr int NQ = Slices<S>::NQ;
+  static constexpr int RPS = TR / (32 * NQ);      // rows per lane per task
+  static constexpr int MAXT = NQ * kMaxQ / NW;    // tasks per warp (upper bound)
+  static constexpr uint32_t COLB = TR * sizeof(S);
+};
+
+// Shared memory (bytes): [full/empty bars 128][h 512][Y 64*k doubles]
+// [task partials 2*NQ*64 doubles][red 64 doubles][stage 0 | stage 1 | ...],
+// a stage = staged columns and vectors, then one TR-vector scratch (s_v).
+template <typename S>
+__host__ __device__ inline size_t ts_smem_fixed(int k) {
+  using L = TSLayout<S>;
+  const size_t ybytes = (size_t)kMaxQ * (size_t)(k > 0 ? k : 1) * sizeof(double);
+  const size_t fixed = 128 + 512 + ybytes + 2 * L::NQ * kMaxQ * sizeof(double) + 64 * sizeof(double);
+  return (fixed + 127) / 128 * 128;
+}
+template <typename S>
+__host__ __device__ inline size_t ts_stage_bytes(int nmat, int w, int nvec) {
+  return (size_t)(nmat * w + nvec + 1) * TSLayout<S>::COLB;
+}
+
+template <typename S>
+__device__ __forceinline__ void ts_issue_tile(const TSArgs<S>& a, unsigned char* stage, uint64_t* full,
+                                              int tile, int lane) {
+  constexpr uint32_t colbytes = TSLayout<S>::COLB;
+  constexpr int TR = TSLayout<S>::TR;
   const int nmc = a.nmat * a.w;
   const int ncopies = nmc + a.nvec;
-  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)ncopies * colbytes);
+  if (lane == 0) mbar_arrive_expect_tx(full, (uint32_t)ncopies * colbytes);
   __syncwarp();
   const int64_t row0 = (int64_t)tile * TR;
   for (int c = lane; c < ncopies; c += 32) {
@@ -86,213 +122,248 @@ __device__ __forceinline__ void ts_issue_tile(const TSArgs<S>& a, unsigned char*
     } else {
       src = a.vec[c - nmc] + row0;
     }
-    bulk_g2s(stage + (size_t)c * colbytes, src, colbytes, bar);
+    bulk_g2s(stage + (size_t)c * colbytes, src, colbytes, full);
   }
 }
 
-// Shared memory layout (bytes): [bars 64][hcoef 512][Y w*k doubles][vtile TR*S][red 2*TR*8][stages]
-template <typename S>
-inline size_t ts_smem_fixed(int w, int k) {
-  constexpr int TR = Tile<S>::TR;
-  size_t ybytes = round_up((size_t)kMaxQ * (size_t)(k > 0 ? k : 1) * sizeof(double), 128);
-  (void)w;
-  return 64 + 512 + ybytes + TR * sizeof(S) + 2 * TR * sizeof(double) + 128;
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+template <int NTHREADS>
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory");
 }
 
 template <typename S, int KIND>
-__global__ void __launch_bounds__(Tile<S>::TR) ts_kernel(TSArgs<S> a) {
-  constexpr int TR = Tile<S>::TR;
-  constexpr int NW = TR / 32;            // warps per CTA
-  constexpr int RPL = TR / 32;           // rows per lane in column-parallel phases
-  constexpr int MAXJ = kMaxQ / NW;       // columns per warp (upper bound)
-  constexpr int KMAX = kMaxK;
-  constexpr uint32_t colbytes = TR * sizeof(S);
+__global__ void __launch_bounds__(Tile<S>::TR + 32) ts_kernel(TSArgs<S> a) {
+  using L = TSLayout<S>;
+  constexpr int TR = L::TR, NW = L::NW, NQ = L::NQ, RPS = L::RPS, MAXT = L::MAXT;
+  constexpr int SLICE = TR / NQ;
+  constexpr bool TASKS = (KIND == TS_PROJ || KIND == TS_INNER || KIND == TS_UPDPROJ || KIND == TS_RESID);
+  constexpr bool TWO = (KIND == TS_INNER || KIND == TS_RESID);
 
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  S* s_h = reinterpret_cast<S*>(smem + 64);          // update coefficients, as S
-  S* s_y = reinterpret_cast<S*>(smem + 64 + 512);    // rotation coefficients / theta, as S
-  const size_t ybytes = round_up((size_t)kMaxQ * (size_t)(a.k > 0 ? a.k : 1) * sizeof(double), 128);
-  S* s_v = reinterpret_cast<S*>(smem + 64 + 512 + ybytes);
-  double* s_red = reinterpret_cast<double*>(smem + 64 + 512 + ybytes + TR * sizeof(S));
-  unsigned char* stages = smem + round_up(64 + 512 + ybytes + TR * sizeof(S) + 2 * TR * sizeof(double), 128);
-  const size_t stage_bytes = (size_t)(a.nmat * a.w + a.nvec) * colbytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + 8;
+  S* s_h = reinterpret_cast<S*>(smem + 128);
+  S* s_y = reinterpret_cast<S*>(smem + 128 + 512);
+  const size_t ybytes = (size_t)kMaxQ * (size_t)(a.k > 0 ? a.k : 1) * sizeof(double);
+  double* s_task = reinterpret_cast<double*>(smem + 128 + 512 + ybytes);   // [2][NQ * kMaxQ]
+  double* s_red = s_task + 2 * NQ * kMaxQ;
+  unsigned char* stages = smem + ts_smem_fixed<S>(a.k);
+  const size_t stage_bytes = ts_stage_bytes<S>(a.nmat, a.w, a.nvec);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool producer = (warp == NW);
   const int w = a.w;
+  const int ntask = NQ * w;
 
-  // coefficients into shared memory
-  if (KIND == TS_UPDPROJ || KIND == TS_UPDNORM || KIND == TS_UPD) {
-    for (int c = tid; c < w; c += TR) s_h[c] = (S)a.hcoef[c];
-  }
-  if (KIND == TS_ROT) {
-    for (int e = tid; e < w * a.k; e += TR) {
-      int c = e / a.k, j = e - c * a.k;
+  if (KIND == TS_UPDPROJ || KIND == TS_UPDNORM || KIND == TS_UPD)
+    for (int c = tid; c < w; c += blockDim.x) s_h[c] = (S)a.hcoef[c];
+  if (KIND == TS_ROT)
+    for (int e = tid; e < w * a.k; e += blockDim.x) {
+      const int c = e / a.k, j = e - c * a.k;
       s_y[e] = (S)a.Y[(int64_t)j * a.ldY + c];
     }
-  }
-  if (KIND == TS_RESID) {
-    for (int j = tid; j < a.k; j += TR) s_y[j] = (S)a.theta[j];
-  }
+  if (KIND == TS_RESID)
+    for (int j = tid; j < a.k; j += blockDim.x) s_y[j] = (S)a.theta[j];
   if (tid == 0) {
-    for (int s = 0; s < a.stages; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NW);
+    }
     fence_mbar_init();
   }
   __syncthreads();
 
   const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  if (warp == 0) {
-    const int pre = my_tiles < a.stages ? my_tiles : a.stages;
-    for (int s = 0; s < pre; ++s) ts_issue_tile(a, stages + s * stage_bytes, &bars[s], blockIdx.x + s * gridDim.x);
-  }
-
-  // per-thread accumulators
-  Acc<S> acc0[MAXJ], acc1[MAXJ];
+  Acc<S> acc0[MAXT], acc1[MAXT];
 #pragma unroll
-  for (int j = 0; j < MAXJ; ++j) { acc0[j].zero(); acc1[j].zero(); }
+  for (int j = 0; j < MAXT; ++j) { acc0[j].zero(); acc1[j].zero(); }
   Acc<S> racc;
   racc.zero();
-  bool timed_out = false;
-  int consumed = 0;
+  int issued_upto = 0;   // producer: tiles issued
+  bool fail = false;
 
-  for (int it = 0; it < my_tiles; ++it) {
-    const int s = it % a.stages;
-    const uint32_t parity = (uint32_t)((it / a.stages) & 1);
-    bool ok = mbar_wait_bounded(&bars[s], parity);
-    if (!__syncthreads_and(ok)) { timed_out = true; break; }
-    consumed = it + 1;
-    const int tile = blockIdx.x + it * gridDim.x;
-    const int64_t row = (int64_t)tile * TR + tid;
-    const S* st = reinterpret_cast<const S*>(stages + s * stage_bytes);
-    const S* m0 = st + (size_t)a.matsel[0] * w * TR;
-    const S* m1 = st + (size_t)a.matsel[1] * w * TR;
-    const S* m2 = st + (size_t)a.matsel[2] * w * TR;
-    const S* vst = st + (size_t)a.nmat * w * TR;   // staged vectors
-
-    if (KIND == TS_PROJ) {
-#pragma unroll
-      for (int j = 0; j < MAXJ; ++j) {
-        const int c = warp + NW * j;
-        if (c < w) {
-#pragma unroll
-          for (int r = 0; r < RPL; ++r) acc0[j].fma(m0[c * TR + lane + 32 * r], vst[lane + 32 * r]);
-        }
-      }
-    } else if (KIND == TS_INNER) {
-      // prologue: v = M (z - rho bg), thread per row
-      const S z = vst[tid];
-      S v;
-      if (a.pmode == PM_GIVEN) {
-        v = vst[TR + tid];
-      } else {
-        const S bg = vst[TR + tid];
-        v = z - (S)a.rho * bg;
-        if (a.pmode == PM_JACOBI) v *= vst[2 * TR + tid];
-        a.vout[row] = v;
-      }
-      s_v[tid] = v;
-      __syncthreads();
-#pragma unroll
-      for (int j = 0; j < MAXJ; ++j) {
-        const int c = warp + NW * j;
-        if (c < w) {
-#pragma unroll
-          for (int r = 0; r < RPL; ++r) {
-            const int i = lane + 32 * r;
-            acc0[j].fma(m0[c * TR + i], vst[i]);
-            acc1[j].fma(m1[c * TR + i], s_v[i]);
-          }
-        }
-      }
-    } else if (KIND == TS_UPDPROJ || KIND == TS_UPDNORM || KIND == TS_UPD) {
-      // v' = v - U h, thread per row
-      S dot = 0;
-      for (int c = 0; c < w; ++c) dot = fmaS(m0[c * TR + tid], s_h[c], dot);
-      const S vn = vst[tid] - dot;
-      a.vout[row] = vn;
-      if (KIND == TS_UPDNORM) racc.fma(vn, vn);
-      if (KIND == TS_UPDPROJ) {
-        s_v[tid] = vn;
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < MAXJ; ++j) {
-          const int c = warp + NW * j;
-          if (c < w) {
-#pragma unroll
-            for (int r = 0; r < RPL; ++r) acc0[j].fma(m1[c * TR + lane + 32 * r], s_v[lane + 32 * r]);
-          }
-        }
-      }
-    } else if (KIND == TS_ROT) {
-      S out[KMAX];
-#pragma unroll
-      for (int j = 0; j < KMAX; ++j) out[j] = 0;
-      for (int c = 0; c < w; ++c) {
-        const S u = m0[c * TR + tid];
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j)
-          if (j < a.k) out[j] = fmaS(u, s_y[c * a.k + j], out[j]);
-      }
-#pragma unroll
-      for (int j = 0; j < KMAX; ++j)
-        if (j < a.k) a.xout[(int64_t)j * a.ld + row] = out[j];
-    } else if (KIND == TS_RESID) {
-#pragma unroll
-      for (int j = 0; j < MAXJ; ++j) {
-        const int c = warp + NW * j;
-        if (c < w) {
-          const S th = s_y[c];
-#pragma unroll
-          for (int r = 0; r < RPL; ++r) {
-            const int i = lane + 32 * r;
-            const S x = m0[c * TR + i];
-            const S rr = m1[c * TR + i] - th * m2[c * TR + i];
-            acc0[j].fma(rr, rr);
-            acc1[j].fma(x, x);
-          }
-        }
-      }
-    } else if (KIND == TS_DOT) {
-      racc.fma(vst[tid], vst[TR + tid]);
-    }
-
-    __syncthreads();   // everyone is done with stage s
-    if (warp == 0 && it + a.stages < my_tiles)
-      ts_issue_tile(a, stages + s * stage_bytes, &bars[s], blockIdx.x + (it + a.stages) * gridDim.x);
-  }
-
-  if (timed_out) {
-    // drain copies still in flight into our shared memory, then report
-    if (tid == 0) atomicOr(a.status, kFlagTimeout);
-    for (int it = consumed; it < my_tiles && it < consumed + a.stages; ++it) {
+  if (producer) {
+    // ---------------- producer warp: keep STAGES tiles in flight
+    for (int it = 0; it < my_tiles; ++it) {
       const int s = it % a.stages;
-      mbar_wait_bounded(&bars[s], (uint32_t)((it / a.stages) & 1));
+      if (it >= a.stages) {
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait_bounded(&empty[s], (uint32_t)(((it / a.stages) - 1) & 1)) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) { fail = true; break; }
+      }
+      ts_issue_tile(a, stages + s * stage_bytes, &full[s], blockIdx.x + it * gridDim.x, lane);
+      issued_upto = it + 1;
     }
-    __syncthreads();
+  } else {
+    // ---------------- consumer warps
+    for (int it = 0; it < my_tiles; ++it) {
+      const int s = it % a.stages;
+      if (!mbar_wait_bounded(&full[s], (uint32_t)((it / a.stages) & 1))) { fail = true; break; }
+      const int tile = blockIdx.x + it * gridDim.x;
+      const int64_t row0 = (int64_t)tile * TR;
+      const S* st = reinterpret_cast<const S*>(stages + s * stage_bytes);
+      const S* m0 = st + (size_t)a.matsel[0] * w * TR;
+      const S* m1 = st + (size_t)a.matsel[1] * w * TR;
+      const S* m2 = st + (size_t)a.matsel[2] * w * TR;
+      const S* vst = st + (size_t)a.nmat * w * TR;                          // staged vectors
+      S* s_v = const_cast<S*>(st) + (size_t)(a.nmat * w + a.nvec) * TR;     // per-stage scratch
+
+      if (KIND == TS_PROJ || KIND == TS_INNER || KIND == TS_RESID) {
+        // TS_INNER: the preconditioned vector for every row this lane touches
+        // (no barrier: each warp forms it for the whole tile; warp k stores
+        // row block k)
+        S vr[NQ][RPS];
+        if (KIND == TS_INNER) {
+#pragma unroll
+          for (int h = 0; h < NQ; ++h)
+#pragma unroll
+            for (int r = 0; r < RPS; ++r) {
+              const int i = h * SLICE + lane + 32 * r;
+              S v;
+              if (a.pmode == PM_GIVEN) {
+                v = vst[TR + i];
+              } else {
+                v = vst[i] - (S)a.rho * vst[TR + i];
+                if (a.pmode == PM_JACOBI) v *= vst[2 * TR + i];
+                if (h * (SLICE / 32) + r == warp) a.vout[row0 + i] = v;
+              }
+              vr[h][r] = v;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < MAXT; ++j) {
+          const int t = warp + NW * j;
+          if (t >= ntask) break;   // warp-uniform branch: no predicated-off FMAs
+          const int c = t / NQ, h = t - c * NQ;
+          const int base = h * SLICE + lane;
+          if (KIND == TS_PROJ) {
+#pragma unroll
+            for (int r = 0; r < RPS; ++r) acc0[j].fma(m0[c * TR + base + 32 * r], vst[base + 32 * r]);
+          } else if (KIND == TS_INNER) {
+#pragma unroll
+            for (int r = 0; r < RPS; ++r) {
+              acc0[j].fma(m0[c * TR + base + 32 * r], vst[base + 32 * r]);
+              S vv = vr[0][r];
+#pragma unroll
+              for (int hh = 1; hh < NQ; ++hh)
+                if (h == hh) vv = vr[hh][r];
+              acc1[j].fma(m1[c * TR + base + 32 * r], vv);
+            }
+          } else {  // TS_RESID
+            const S th = s_y[c];
+#pragma unroll
+            for (int r = 0; r < RPS; ++r) {
+              const S x = m0[c * TR + base + 32 * r];
+              const S rr = m1[c * TR + base + 32 * r] - th * m2[c * TR + base + 32 * r];
+              acc0[j].fma(rr, rr);
+              acc1[j].fma(x, x);
+            }
+          }
+        }
+      } else if (KIND == TS_UPDPROJ || KIND == TS_UPDNORM || KIND == TS_UPD) {
+        // v' = v - U h, thread per row, two chains
+        S d0 = 0, d1 = 0;
+        int c = 0;
+        for (; c + 1 < w; c += 2) {
+          d0 = fmaS(m0[c * TR + tid], s_h[c], d0);
+          d1 = fmaS(m0[(c + 1) * TR + tid], s_h[c + 1], d1);
+        }
+        if (c < w) d0 = fmaS(m0[c * TR + tid], s_h[c], d0);
+        const S vn = vst[tid] - (d0 + d1);
+        a.vout[row0 + tid] = vn;
+        if (KIND == TS_UPDNORM) racc.fma(vn, vn);
+        if (KIND == TS_UPDPROJ) {
+          s_v[tid] = vn;
+          consumer_sync<TR>();
+#pragma unroll
+          for (int j = 0; j < MAXT; ++j) {
+            const int t = warp + NW * j;
+            if (t >= ntask) break;
+            const int cc = t / NQ, h = t - cc * NQ;
+            const int base = h * SLICE + lane;
+#pragma unroll
+            for (int r = 0; r < RPS; ++r) acc0[j].fma(m1[cc * TR + base + 32 * r], s_v[base + 32 * r]);
+          }
+        }
+      } else if (KIND == TS_ROT) {
+        // outputs in chunks of KC so no FMA is spent on columns past k
+        constexpr int KC = 4;
+        for (int j0 = 0; j0 < a.k; j0 += KC) {
+          if (j0 + KC <= a.k) {
+            S out[KC];
+#pragma unroll
+            for (int u = 0; u < KC; ++u) out[u] = 0;
+            for (int c = 0; c < w; ++c) {
+              const S uu = m0[c * TR + tid];
+#pragma unroll
+              for (int u = 0; u < KC; ++u) out[u] = fmaS(uu, s_y[c * a.k + j0 + u], out[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < KC; ++u) a.xout[(int64_t)(j0 + u) * a.ld + row0 + tid] = out[u];
+          } else {
+            for (int j = j0; j < a.k; ++j) {
+              S o = 0;
+              for (int c = 0; c < w; ++c) o = fmaS(m0[c * TR + tid], s_y[c * a.k + j], o);
+              a.xout[(int64_t)j * a.ld + row0 + tid] = o;
+            }
+          }
+        }
+      } else if (KIND == TS_DOT) {
+        racc.fma(vst[tid], vst[TR + tid]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
   }
+
+  // ---------------- drain and report a timeout
+  if (fail) atomicOr(a.status, kFlagTimeout);
+  if (producer && fail) {
+    // copies issued but possibly still in flight into our shared memory
+    for (int it = issued_upto - a.stages; it < issued_upto; ++it) {
+      if (it < 0) continue;
+      const int s = it % a.stages;
+      if (lane == 0) mbar_wait_bounded(&full[s], (uint32_t)((it / a.stages) & 1));
+    }
+  }
+  __syncthreads();
 
   // ---------------- per-CTA partials
   double* part = a.partials + (size_t)blockIdx.x * a.pstride;
-  if (KIND == TS_PROJ || KIND == TS_INNER || KIND == TS_UPDPROJ || KIND == TS_RESID) {
+  if (TASKS) {
+    if (!producer) {
 #pragma unroll
-    for (int j = 0; j < MAXJ; ++j) {
-      const int c = warp + NW * j;
-      if (c < w) {  // warp-uniform
+      for (int j = 0; j < MAXT; ++j) {
+        const int t = warp + NW * j;
+        if (t >= ntask) break;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
           acc0[j].shfl_down_add(off);
-          if (KIND == TS_INNER || KIND == TS_RESID) acc1[j].shfl_down_add(off);
+          if (TWO) acc1[j].shfl_down_add(off);
         }
         if (lane == 0) {
-          part[c] = acc0[j].value();
-          if (KIND == TS_INNER || KIND == TS_RESID) part[kMaxQ + c] = acc1[j].value();
+          s_task[t] = acc0[j].value();
+          if (TWO) s_task[NQ * kMaxQ + t] = acc1[j].value();
         }
       }
+    }
+    __syncthreads();
+    for (int o = tid; o < (TWO ? 2 : 1) * w; o += blockDim.x) {
+      const int r = o / w, c = o - r * w;
+      double t = 0.0;
+#pragma unroll
+      for (int h = 0; h < NQ; ++h) t += s_task[r * NQ * kMaxQ + c * NQ + h];
+      part[r * kMaxQ + c] = t;
     }
   } else if (KIND == TS_UPDNORM || KIND == TS_DOT) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) racc.shfl_down_add(off);
-    if (lane == 0) s_red[warp] = racc.value();
+    if (lane == 0) s_red[warp] = producer ? 0.0 : racc.value();
     __syncthreads();
     if (tid == 0) {
       double t = 0.0;
@@ -307,10 +378,10 @@ __global__ void __launch_bounds__(Tile<S>::TR) ts_kernel(TSArgs<S> a) {
   // order, then a fixed shuffle tree combines the lanes (deterministic).
   if (!last_block_arrive(a.counter)) return;
   const int nb = gridDim.x;
-  if (KIND == TS_PROJ || KIND == TS_INNER || KIND == TS_UPDPROJ || KIND == TS_RESID) {
-    const bool two = (KIND == TS_INNER || KIND == TS_RESID);
-    const int nout = two ? 2 * w : w;   // outputs o < w -> out0[o], else out1[o - w]
-    for (int o0 = warp * 4; o0 < nout; o0 += NW * 4) {
+  const int nwarps = blockDim.x / 32;
+  if (TASKS) {
+    const int nout = TWO ? 2 * w : w;   // outputs o < w -> out0[o], else out1[o - w]
+    for (int o0 = warp * 4; o0 < nout; o0 += nwarps * 4) {
       double t[4] = {0.0, 0.0, 0.0, 0.0};
       int col[4];
 #pragma unroll

@@ -20,7 +20,7 @@ void launch_kind(const Ctx& c, TSArgs<S>& a, size_t smem, int grid) {
                                         (int)kSmemMax));
     configured = true;
   }
-  ts_kernel<S, KIND><<<grid, Tile<S>::TR, smem, c.stream>>>(a);
+  ts_kernel<S, KIND><<<grid, Tile<S>::TR + 32, smem, c.stream>>>(a);
   check_launch("ts_kernel");
 }
 
@@ -31,14 +31,15 @@ void run(const Ctx& c, TSArgs<S> a, int kind) {
   if (a.w < 0 || a.w > kMaxQ) throw Error(TRPLK_EINVAL, "basis width out of range");
   a.ntiles = (int)(a.ld / TR);
   if (a.ntiles == 0) return;
-  const size_t fixed = ts_smem_fixed<S>(a.w, a.k);
-  const size_t stage = (size_t)(a.nmat * a.w + a.nvec) * TR * sizeof(S);
-  int stages = stage == 0 ? 1 : (int)std::min<size_t>(4, (kSmemMax - fixed) / stage);
+  const size_t fixed = ts_smem_fixed<S>(a.k);
+  const size_t stage = ts_stage_bytes<S>(a.nmat, a.w, a.nvec);
+  int stages = (int)std::min<size_t>(4, (kSmemMax - fixed) / stage);
   if (stages < 1) throw Error(TRPLK_EINVAL, "tile does not fit in shared memory");
   a.stages = stages;
   const size_t smem = fixed + (size_t)stages * stage;
+  const int threads = TR + 32;
   int per_sm = (int)std::max<size_t>(1, kSmemPerSM / (smem + 1024));
-  per_sm = std::min(per_sm, 2048 / TR);
+  per_sm = std::min(per_sm, 2048 / threads);
   int grid = std::min<int64_t>(a.ntiles, (int64_t)c.sms * per_sm);
   grid = std::min(grid, kMaxPartials);
   a.partials = c.partials;
@@ -46,6 +47,12 @@ void run(const Ctx& c, TSArgs<S> a, int kind) {
   a.counter = c.counter;
   a.status = c.status;
   a.kind = kind;
+  // algorithmic bytes: every staged column and vector once, plus the outputs
+  double bytes = (double)(a.nmat * a.w + a.nvec) * a.ld * sizeof(S);
+  if (kind == TS_INNER && a.pmode != PM_GIVEN) bytes += (double)a.ld * sizeof(S);
+  if (kind == TS_UPDPROJ || kind == TS_UPDNORM || kind == TS_UPD) bytes += (double)a.ld * sizeof(S);
+  if (kind == TS_ROT) bytes += (double)a.k * a.ld * sizeof(S);
+  ProfScope ps(c, PK_TS_PROJ + kind, bytes);
   switch (kind) {
     case TS_PROJ: launch_kind<S, TS_PROJ>(c, a, smem, grid); break;
     case TS_INNER: launch_kind<S, TS_INNER>(c, a, smem, grid); break;
