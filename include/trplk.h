@@ -225,6 +225,28 @@ trplk_status trplk_check_residuals(trplk_handle* h, const trplk_csr* A, const tr
                                    int64_t ld, int p, const double* X, const double* theta,
                                    double normA, double* resid);
 
+/* The projection of trplk_project, h = BU[:, 0:w]^T v, for callers that
+ * cannot let the library allocate device memory.  The paper has no
+ * counterpart: this is an interface for two kinds of caller -- processes that
+ * have already planned all device memory through their own pool (a
+ * cudaMalloc here would fail or break that plan) and latency-critical loops
+ * that cannot afford the device synchronisation an allocation may cause.
+ * Needs no handle; runs on `cuda_stream` (NULL = legacy default stream) of
+ * the current device and returns after it finished.  Arguments as for
+ * trplk_project (dtype, n, ld % 256 == 0 with zero padding rows, 1 <= w <= 64,
+ * device pointers, hout double[w]).
+ * Scratch: one fixed __device__ array inside the library holding the partial
+ * sums of at most 256 CTAs (256 KiB + 256 bytes), kept by every GPU that
+ * loads the library until the process exits; the call never uses more CTAs,
+ * so any n fits, and w > 64 returns TRPLK_EINVAL.  The array is shared by all
+ * calls and keeps the last call's contents (the call clears the words that
+ * must start at zero); calls whose kernels overlap on the GPU race on it and
+ * must be serialised by the caller.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  No cudaMalloc, cudaFree or other allocating call. */
+trplk_status trplk_project_noalloc(int dtype, int64_t n, int64_t ld, int w, const void* BU,
+                                   const void* v, double* hout, void* cuda_stream);
+
 /* ------------------------------------------------------------------------
  * Per-kernel profiling (measurement support, not part of the method).
  * ---------------------------------------------------------------------- */

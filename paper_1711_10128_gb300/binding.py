@@ -74,6 +74,7 @@ def _load():
         "trplk_residual_norms": (st, [vp, i32, i64, i64, i32, vp, vp, vp, vp, vp, vp]),
         "trplk_start_block": (st, [vp, i64, i64, i32, C.c_uint64, vp]),
         "trplk_check_residuals": (st, [vp, C.POINTER(trplk_csr), C.POINTER(trplk_csr), i64, i32, vp, vp, dbl, vp]),
+        "trplk_project_noalloc": (st, [i32, i64, i64, i32, vp, vp, vp, vp]),
         "trplk_profile": (st, [vp, i32]),
         "trplk_profile_read": (st, [vp, i32, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "trplk_profile_kind_name": (C.c_char_p, [i32]),
@@ -210,6 +211,14 @@ def trplk_start_block(h, n, ld, k, seed, X):
 def trplk_check_residuals(h, A, B, ld, p, X, theta, normA, resid):
     return h.check(LIB.trplk_check_residuals(h.h, C.byref(A), C.byref(B) if B is not None else None, ld, p, ptr(X),
                                              ptr(theta), float(normA), ptr(resid)))
+
+
+def trplk_project_noalloc(dtype, n, ld, w, BU, v, hout, stream=None):
+    """h = BU^T v without any device allocation (status code; raises on error)."""
+    rc = LIB.trplk_project_noalloc(dtype, n, ld, w, ptr(BU), ptr(v), ptr(hout), stream)
+    if rc != OK:
+        raise TrplkError(rc, "trplk_project_noalloc failed")
+    return rc
 
 
 def trplk_profile(h, enable):
