@@ -115,6 +115,18 @@ template <> struct Acc<float> {
   }
 };
 
+// AccFast<S>: plain accumulation in S.  Used only for the first CGS pass of
+// the FP32 path, whose rounding errors the second (compensated) pass removes.
+template <typename S> struct AccFast;
+template <> struct AccFast<double> : Acc<double> {};
+template <> struct AccFast<float> {
+  float p;
+  __device__ __forceinline__ void zero() { p = 0.f; }
+  __device__ __forceinline__ void fma(float a, float b) { p = fmaf(a, b, p); }
+  __device__ __forceinline__ double value() const { return (double)p; }
+  __device__ __forceinline__ void shfl_down_add(int off) { p += __shfl_down_sync(0xffffffffu, p, off); }
+};
+
 // ----------------------------------------------------------------- device: mbarrier + bulk copy
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -87,6 +87,11 @@ struct DevCsr {
   const int64_t* rowptr = nullptr;
   const int32_t* col = nullptr;
   const S* val = nullptr;
+  // optional SELL-32 copy (slices of 32 rows, entries column-major within a
+  // slice, padded with zeros); used by the matvec when present
+  const int64_t* sl_ptr = nullptr;   // [nslices + 1], multiples of 32
+  const int32_t* sl_col = nullptr;
+  const S* sl_val = nullptr;
 };
 
 // ---- SpMV (spmv.cu)
@@ -98,6 +103,13 @@ void spmv(const Ctx& c, const DevCsr<S>& A, const S* x, S* y);
 template <typename S>
 void spmv_scaled(const Ctx& c, const DevCsr<S>& A, const S* x, const double* scale, S* y, S* g,
                  const S* bx, S* bg);
+
+// SELL-32 construction: lens[s] = longest row of slice s; then, given the
+// slice offsets, scatter column indices (when col != nullptr) and values.
+void sell_lengths(const Ctx& c, int64_t n, const int64_t* rowptr, int32_t* lens);
+template <typename S>
+void sell_fill(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+               const int64_t* sl_ptr, int32_t* sl_col, S* sl_val);
 
 // ---- tall-skinny passes (ts.cu).  All vectors have ld rows (zero padded).
 template <typename S>

@@ -145,6 +145,38 @@ __global__ void set_diag_block_kernel(double* T, int ldT, int k, const double* t
   }
 }
 
+// Build the SELL-32 copy of a device CSR (values from the FP64 array; an
+// FP32 copy too when f32 != nullptr) unless padding would add more than 25%.
+void attach_sell(trplk_handle* h, DevCsr<double>& d, const std::string& tag, DevCsr<float>* f32) {
+  const Ctx& c = h->ctx;
+  const int64_t nslices = (d.n + 31) / 32;
+  auto* lens = static_cast<int32_t*>(h->get(tag + ".sl_len", nslices * sizeof(int32_t)));
+  sell_lengths(c, d.n, d.rowptr, lens);
+  std::vector<int32_t> hl(nslices);
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(hl.data(), lens, nslices * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  h->sync();
+  std::vector<int64_t> ptr(nslices + 1, 0);
+  for (int64_t s = 0; s < nslices; ++s) ptr[s + 1] = ptr[s] + 32 * (int64_t)hl[s];
+  const int64_t padded = ptr[nslices];
+  if ((double)padded > 1.25 * (double)d.nnz + 32.0 * nslices) return;
+  auto* sp = static_cast<int64_t*>(h->get(tag + ".sl_ptr", (nslices + 1) * sizeof(int64_t)));
+  auto* sc = static_cast<int32_t*>(h->get(tag + ".sl_col", padded * sizeof(int32_t)));
+  auto* sv = static_cast<double*>(h->get(tag + ".sl_val", padded * sizeof(double)));
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(sp, ptr.data(), (nslices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
+  sell_fill<double>(c, d.n, d.rowptr, d.col, d.val, sp, sc, sv);
+  d.sl_ptr = sp;
+  d.sl_col = sc;
+  d.sl_val = sv;
+  if (f32) {
+    auto* svf = static_cast<float*>(h->get(tag + ".sl_valf", padded * sizeof(float)));
+    sell_fill<float>(c, d.n, d.rowptr, d.col, d.val, sp, nullptr, svf);
+    f32->sl_ptr = sp;
+    f32->sl_col = sc;
+    f32->sl_val = svf;
+  }
+  h->sync();   // ptr (host vector) must stay alive until its copy finished
+}
+
 // Upload or wrap a caller's CSR; `tag` names the workspace slots.
 Operator make_operator(trplk_handle* h, const trplk_csr* M, const std::string& tag, bool need_f32) {
   Operator op;
@@ -196,6 +228,7 @@ Operator make_operator(trplk_handle* h, const trplk_csr* M, const std::string& t
     convert<float, double>(c, op.nnz, op.d.val, vf);
     op.f = DevCsr<float>{op.n, op.nnz, op.d.rowptr, op.d.col, vf};
   }
+  attach_sell(h, op.d, tag, need_f32 ? &op.f : nullptr);
   return op;
 }
 
@@ -739,9 +772,16 @@ trplk_status trplk_spmv(trplk_handle* h, const trplk_csr* A, const void* x, void
     if (!A || !A->on_device || !x || !y || A->n < 1) throw Error(TRPLK_EINVAL, "bad spmv arguments");
     if (x == y) throw Error(TRPLK_EINVAL, "y must not alias x");
     if (A->dtype == TRPLK_F64) {
-      spmv<double>(h->ctx, dev_csr64(A), static_cast<const double*>(x), static_cast<double*>(y));
+      DevCsr<double> a = dev_csr64(A);
+      attach_sell(h, a, "step.spmv", nullptr);
+      spmv<double>(h->ctx, a, static_cast<const double*>(x), static_cast<double*>(y));
     } else if (A->dtype == TRPLK_F32) {
       DevCsr<float> a{A->n, A->nnz, A->rowptr, A->col, static_cast<const float*>(A->val)};
+      // the FP32 SELL copy is built from an FP64 view of the same values
+      double* v64 = static_cast<double*>(h->get("step.spmv.v64", A->nnz * sizeof(double)));
+      convert<double, float>(h->ctx, A->nnz, static_cast<const float*>(A->val), v64);
+      DevCsr<double> d{A->n, A->nnz, A->rowptr, A->col, v64};
+      attach_sell(h, d, "step.spmv", &a);
       spmv<float>(h->ctx, a, static_cast<const float*>(x), static_cast<float*>(y));
     } else {
       throw Error(TRPLK_EINVAL, "bad dtype");

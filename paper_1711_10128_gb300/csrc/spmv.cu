@@ -1,6 +1,8 @@
 // Sparse matrix-vector products and small elementwise kernels.
 //
-// SpMV (eq. (UpdateT), z = A g): CSR-stream, one thread per row.  A CTA owns
+// SpMV (eq. (UpdateT), z = A g).  Operators whose rows have similar lengths
+// (stencils, FEM) are converted to SELL-32 at set-up and multiplied by
+// sell_spmv_kernel below; others use CSR-stream, one thread per row.  A CTA owns
 // 256 consecutive rows; it streams the values and column indices of those
 // rows into shared memory with coalesced loads (the rows are contiguous in
 // CSR, so the whole block is one contiguous range), then each thread forms its
@@ -89,10 +91,83 @@ __global__ void __launch_bounds__(kRows) spmv_kernel(int64_t n, const int64_t* _
   }
 }
 
+// SELL-32 matvec: one warp per 32-row slice, one lane per row.  The slice's
+// entries are stored column-major, so every load of values and column indices
+// is one coalesced 128/256-byte transaction and independent of the others;
+// no row-pointer chase and no shared-memory staging.
+template <typename S, bool SCALED>
+__global__ void __launch_bounds__(256) sell_spmv_kernel(int64_t n, int64_t nslices,
+                                                        const int64_t* __restrict__ sl_ptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const S* __restrict__ val, const S* __restrict__ x,
+                                                        S* __restrict__ y, const double* __restrict__ scale,
+                                                        S* __restrict__ g, const S* __restrict__ bx,
+                                                        S* __restrict__ bg) {
+  const int64_t slice = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (slice >= nslices) return;
+  const int64_t base = sl_ptr[slice];
+  const int len = (int)((sl_ptr[slice + 1] - base) >> 5);
+  const S* vp = val + base + lane;
+  const int32_t* cp = col + base + lane;
+  S sum = 0;
+  int j = 0;
+  for (; j + 4 <= len; j += 4) {
+    const int32_t c0 = __ldg(cp + 32 * j), c1 = __ldg(cp + 32 * (j + 1));
+    const int32_t c2 = __ldg(cp + 32 * (j + 2)), c3 = __ldg(cp + 32 * (j + 3));
+    const S v0 = __ldg(vp + 32 * j), v1 = __ldg(vp + 32 * (j + 1));
+    const S v2 = __ldg(vp + 32 * (j + 2)), v3 = __ldg(vp + 32 * (j + 3));
+    const S x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+    sum = fmaS(v0, x0, sum);
+    sum = fmaS(v1, x1, sum);
+    sum = fmaS(v2, x2, sum);
+    sum = fmaS(v3, x3, sum);
+  }
+  if (j < len) {   // remainder of 1..3 entries, loads issued together
+    const int r = len - j;
+    const int32_t c0 = __ldg(cp + 32 * j);
+    const int32_t c1 = r > 1 ? __ldg(cp + 32 * (j + 1)) : c0;
+    const int32_t c2 = r > 2 ? __ldg(cp + 32 * (j + 2)) : c0;
+    const S v0 = __ldg(vp + 32 * j);
+    const S v1 = r > 1 ? __ldg(vp + 32 * (j + 1)) : (S)0;
+    const S v2 = r > 2 ? __ldg(vp + 32 * (j + 2)) : (S)0;
+    const S x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2);
+    sum = fmaS(v0, x0, sum);
+    if (r > 1) sum = fmaS(v1, x1, sum);
+    if (r > 2) sum = fmaS(v2, x2, sum);
+  }
+  const int64_t row = slice * 32 + lane;
+  if (row < n) {
+    if (SCALED) {
+      const S s = (S)(*scale);
+      y[row] = s * sum;
+      g[row] = s * x[row];
+      if (bx) bg[row] = s * bx[row];
+    } else {
+      y[row] = sum;
+    }
+  }
+}
+
 template <typename S>
 void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const double* scale, S* g,
                  const S* bx, S* bg, bool scaled) {
   if (A.n == 0) return;
+  if (A.sl_ptr) {
+    const int64_t nslices = (A.n + 31) / 32;
+    const int64_t blocks = (nslices * 32 + 255) / 256;
+    double bytes = (double)A.nnz * (sizeof(S) + 4) + (double)(nslices + 1) * 8 + 2.0 * A.n * sizeof(S);
+    if (scaled) bytes += (double)A.n * sizeof(S) * (bx ? 3 : 1);
+    ProfScope ps(c, scaled ? PK_SPMV_SCALED : PK_SPMV, bytes);
+    if (scaled)
+      sell_spmv_kernel<S, true><<<(unsigned)blocks, 256, 0, c.stream>>>(A.n, nslices, A.sl_ptr, A.sl_col, A.sl_val,
+                                                                         x, y, scale, g, bx, bg);
+    else
+      sell_spmv_kernel<S, false><<<(unsigned)blocks, 256, 0, c.stream>>>(A.n, nslices, A.sl_ptr, A.sl_col, A.sl_val,
+                                                                          x, y, nullptr, nullptr, nullptr, nullptr);
+    check_launch("sell_spmv_kernel");
+    return;
+  }
   constexpr int CH = Chunk<S>::CH;
   const size_t smem = CH * (sizeof(S) + sizeof(int32_t));
   const int64_t blocks = (A.n + kRows - 1) / kRows;
@@ -175,6 +250,40 @@ __global__ void jacobi_dinv_kernel(int64_t n, const int64_t* __restrict__ rowptr
   }
 }
 
+__global__ void sell_lengths_kernel(int64_t n, const int64_t* __restrict__ rowptr, int32_t* __restrict__ lens) {
+  const int64_t slice = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = slice * 32 + lane;
+  int len = row < n ? (int)(rowptr[row + 1] - rowptr[row]) : 0;
+  for (int off = 16; off > 0; off >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, off));
+  if (lane == 0 && slice * 32 < n) lens[slice] = len;
+}
+
+template <typename S>
+__global__ void sell_fill_kernel(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                 const double* __restrict__ val, const int64_t* __restrict__ sl_ptr,
+                                 int32_t* __restrict__ sl_col, S* __restrict__ sl_val) {
+  const int64_t slice = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (slice * 32 >= n) return;
+  const int64_t row = slice * 32 + lane;
+  const int64_t base = sl_ptr[slice];
+  const int len = (int)((sl_ptr[slice + 1] - base) >> 5);
+  const int64_t rs = row < n ? rowptr[row] : 0;
+  const int rl = row < n ? (int)(rowptr[row + 1] - rs) : 0;
+  const int32_t pad_col = (int32_t)(row < n ? row : 0);
+  for (int j = 0; j < len; ++j) {
+    const int64_t o = base + 32 * (int64_t)j + lane;
+    if (j < rl) {
+      if (sl_col) sl_col[o] = col[rs + j];
+      sl_val[o] = (S)val[rs + j];
+    } else {
+      if (sl_col) sl_col[o] = pad_col;
+      sl_val[o] = (S)0;
+    }
+  }
+}
+
 inline unsigned grid_for(const Ctx& c, int64_t count) {
   int64_t g = (count + 255) / 256;
   int64_t cap = (int64_t)c.sms * 8;
@@ -230,6 +339,27 @@ void axpby_shift(const Ctx& c, int64_t ld, const S* x, const S* y, double rho, S
   check_launch("axpby_shift");
 }
 
+void sell_lengths(const Ctx& c, int64_t n, const int64_t* rowptr, int32_t* lens) {
+  const int64_t nslices = (n + 31) / 32;
+  ProfScope ps(c, PK_OTHER, 0.0);
+  sell_lengths_kernel<<<(unsigned)((nslices * 32 + 255) / 256), 256, 0, c.stream>>>(n, rowptr, lens);
+  check_launch("sell_lengths");
+}
+
+template <typename S>
+void sell_fill(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+               const int64_t* sl_ptr, int32_t* sl_col, S* sl_val) {
+  const int64_t nslices = (n + 31) / 32;
+  ProfScope ps(c, PK_OTHER, 0.0);
+  sell_fill_kernel<S><<<(unsigned)((nslices * 32 + 255) / 256), 256, 0, c.stream>>>(n, rowptr, col, val, sl_ptr,
+                                                                                    sl_col, sl_val);
+  check_launch("sell_fill");
+}
+
+template void sell_fill<double>(const Ctx&, int64_t, const int64_t*, const int32_t*, const double*, const int64_t*,
+                                int32_t*, double*);
+template void sell_fill<float>(const Ctx&, int64_t, const int64_t*, const int32_t*, const double*, const int64_t*,
+                               int32_t*, float*);
 template void spmv<double>(const Ctx&, const DevCsr<double>&, const double*, double*);
 template void spmv<float>(const Ctx&, const DevCsr<float>&, const float*, float*);
 template void spmv_scaled<double>(const Ctx&, const DevCsr<double>&, const double*, const double*, double*,

@@ -9,18 +9,22 @@
 //    copy per column segment and per vector segment -- and NW = TR/32
 //    consumer warps compute on it; every stage has a "full" mbarrier
 //    (transaction bytes) and an "empty" mbarrier (one arrival per consumer
-//    warp), so consumers run ahead by up to STAGES tiles and the producer
+//    warp), so consumers run ahead by up to STAGES (<= 8) tiles and the producer
 //    refills a stage as soon as the last consumer has left it;
 //  * compute reads shared memory only: thread-per-row for the updates
 //    v <- v - U h, and balanced (column, row-slice) tasks for the projections
 //    U^T v, each task with its own accumulator;
 //  * projections accumulate in FP64 (double data) or Dot2-compensated FP32
-//    (float data), are reduced per CTA and then summed in CTA order by the
-//    last CTA to finish (deterministic, no floating-point atomics).
+//    (float data) -- except the first CGS pass of the float path, accumulated
+//    plainly in FP32 because the second, compensated pass removes its error --
+//    are reduced per CTA and then summed in CTA order by the last CTA to
+//    finish (deterministic, no floating-point atomics).
 // Rows n..ld-1 of every array are zero, so whole tiles are always copied.
 // Every wait is bounded: a stage that never arrives sets kFlagTimeout, the
 // kernel drains the copies it issued and returns.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace trplk {
@@ -135,8 +139,13 @@ __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory");
 }
 
+// Two CTAs per SM for the float path (<= 113 registers), where the FP32
+// pipes need the extra warps to hide the compensated-sum latency chains.
+template <typename S> struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<float> { static constexpr int value = 2; };
+
 template <typename S, int KIND>
-__global__ void __launch_bounds__(Tile<S>::TR + 32) ts_kernel(TSArgs<S> a) {
+__global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kernel(TSArgs<S> a) {
   using L = TSLayout<S>;
   constexpr int TR = L::TR, NW = L::NW, NQ = L::NQ, RPS = L::RPS, MAXT = L::MAXT;
   constexpr int SLICE = TR / NQ;
@@ -178,7 +187,11 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32) ts_kernel(TSArgs<S> a) {
   __syncthreads();
 
   const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  Acc<S> acc0[MAXT], acc1[MAXT];
+  // TS_INNER's second right-hand side is the first CGS pass: plain
+  // accumulation (its error is removed by the compensated second pass)
+  using Acc1 = typename std::conditional<KIND == TS_INNER, AccFast<S>, Acc<S>>::type;
+  Acc<S> acc0[MAXT];
+  Acc1 acc1[MAXT];
 #pragma unroll
   for (int j = 0; j < MAXT; ++j) { acc0[j].zero(); acc1[j].zero(); }
   Acc<S> racc;

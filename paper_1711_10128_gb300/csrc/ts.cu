@@ -12,14 +12,45 @@ namespace {
 constexpr size_t kSmemMax = 232448 - 1024;   // opt-in shared memory per CTA less static use
 constexpr size_t kSmemPerSM = 233472;        // shared memory per SM
 
+// CTAs of one instantiation that fit on an SM by registers and threads.
 template <typename S, int KIND>
-void launch_kind(const Ctx& c, TSArgs<S>& a, size_t smem, int grid) {
-  static bool configured = false;   // one attribute call per instantiation
-  if (!configured) {
+int regs_limit() {
+  static int lim = 0;
+  if (!lim) {
+    cudaFuncAttributes fa;
+    TRPLK_CUDA_TRY(cudaFuncGetAttributes(&fa, ts_kernel<S, KIND>));
+    const int threads = Tile<S>::TR + 32;
+    const int regs = std::max(fa.numRegs, 1) * threads;
+    lim = std::max(1, std::min(65536 / regs, 2048 / threads));
     TRPLK_CUDA_TRY(cudaFuncSetAttribute(ts_kernel<S, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)kSmemMax));
-    configured = true;
   }
+  return lim;
+}
+
+template <typename S, int KIND>
+void launch_kind(const Ctx& c, TSArgs<S>& a, size_t fixed, size_t stage, double bytes) {
+  // Most CTAs per SM that still keep >= 4 stages each (latency hiding needs
+  // both: several producer/consumer groups and ~100 KB in flight per SM),
+  // then as many stages as fit, up to 8.
+  const int lim = regs_limit<S, KIND>();
+  int per_sm = 1, stages = 0;
+  for (int cand = lim; cand >= 1; --cand) {
+    const size_t per_cta = std::min<size_t>(kSmemMax, kSmemPerSM / cand - 1024);
+    if (per_cta <= fixed) continue;
+    const int st = (int)std::min<size_t>(8, (per_cta - fixed) / stage);
+    if (st >= 4 || (cand == 1 && st >= 1)) {
+      per_sm = cand;
+      stages = st;
+      break;
+    }
+  }
+  if (stages < 1) throw Error(TRPLK_EINVAL, "tile does not fit in shared memory");
+  a.stages = stages;
+  const size_t smem = fixed + (size_t)stages * stage;
+  int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)c.sms * per_sm);
+  grid = std::min(grid, kMaxPartials);
+  ProfScope ps(c, PK_TS_PROJ + KIND, bytes);
   ts_kernel<S, KIND><<<grid, Tile<S>::TR + 32, smem, c.stream>>>(a);
   check_launch("ts_kernel");
 }
@@ -33,15 +64,6 @@ void run(const Ctx& c, TSArgs<S> a, int kind) {
   if (a.ntiles == 0) return;
   const size_t fixed = ts_smem_fixed<S>(a.k);
   const size_t stage = ts_stage_bytes<S>(a.nmat, a.w, a.nvec);
-  int stages = (int)std::min<size_t>(4, (kSmemMax - fixed) / stage);
-  if (stages < 1) throw Error(TRPLK_EINVAL, "tile does not fit in shared memory");
-  a.stages = stages;
-  const size_t smem = fixed + (size_t)stages * stage;
-  const int threads = TR + 32;
-  int per_sm = (int)std::max<size_t>(1, kSmemPerSM / (smem + 1024));
-  per_sm = std::min(per_sm, 2048 / threads);
-  int grid = std::min<int64_t>(a.ntiles, (int64_t)c.sms * per_sm);
-  grid = std::min(grid, kMaxPartials);
   a.partials = c.partials;
   a.pstride = kPartialStride;
   a.counter = c.counter;
@@ -52,16 +74,15 @@ void run(const Ctx& c, TSArgs<S> a, int kind) {
   if (kind == TS_INNER && a.pmode != PM_GIVEN) bytes += (double)a.ld * sizeof(S);
   if (kind == TS_UPDPROJ || kind == TS_UPDNORM || kind == TS_UPD) bytes += (double)a.ld * sizeof(S);
   if (kind == TS_ROT) bytes += (double)a.k * a.ld * sizeof(S);
-  ProfScope ps(c, PK_TS_PROJ + kind, bytes);
   switch (kind) {
-    case TS_PROJ: launch_kind<S, TS_PROJ>(c, a, smem, grid); break;
-    case TS_INNER: launch_kind<S, TS_INNER>(c, a, smem, grid); break;
-    case TS_UPDPROJ: launch_kind<S, TS_UPDPROJ>(c, a, smem, grid); break;
-    case TS_UPDNORM: launch_kind<S, TS_UPDNORM>(c, a, smem, grid); break;
-    case TS_UPD: launch_kind<S, TS_UPD>(c, a, smem, grid); break;
-    case TS_ROT: launch_kind<S, TS_ROT>(c, a, smem, grid); break;
-    case TS_RESID: launch_kind<S, TS_RESID>(c, a, smem, grid); break;
-    case TS_DOT: launch_kind<S, TS_DOT>(c, a, smem, grid); break;
+    case TS_PROJ: launch_kind<S, TS_PROJ>(c, a, fixed, stage, bytes); break;
+    case TS_INNER: launch_kind<S, TS_INNER>(c, a, fixed, stage, bytes); break;
+    case TS_UPDPROJ: launch_kind<S, TS_UPDPROJ>(c, a, fixed, stage, bytes); break;
+    case TS_UPDNORM: launch_kind<S, TS_UPDNORM>(c, a, fixed, stage, bytes); break;
+    case TS_UPD: launch_kind<S, TS_UPD>(c, a, fixed, stage, bytes); break;
+    case TS_ROT: launch_kind<S, TS_ROT>(c, a, fixed, stage, bytes); break;
+    case TS_RESID: launch_kind<S, TS_RESID>(c, a, fixed, stage, bytes); break;
+    case TS_DOT: launch_kind<S, TS_DOT>(c, a, fixed, stage, bytes); break;
     default: throw Error(TRPLK_EINVAL, "unknown tall-skinny kind");
   }
 }

@@ -10,8 +10,9 @@ residuals (recomputed by the oracle's own matvec) and the matvec accounting.
 Tolerances: FP64 kernels 1e-12 relative to the natural scale of the quantity
 (rounding-order differences of sums of <= n terms, n <= 10^5); FP32 storage
 kernels compare with the oracle evaluated on the same float inputs, with the
-compensated (Dot2) accumulations held to 1e-12 and FP32 arithmetic to 1e-6;
-converged eigenvalues 1e-10 relative (the required FP64 parity).
+compensated (Dot2) accumulations held to 1e-12, the plainly accumulated first
+CGS pass to n u (u = 2^-24) and FP32 arithmetic to 1e-6; converged
+eigenvalues 1e-10 relative (the required FP64 parity).
 """
 import math
 
@@ -170,9 +171,11 @@ def test_inner_project_fp32_compensated(lib, h, n, w):
     exact_t = U64.T @ z.astype(np.float64)
     mag = np.abs(U64).T @ np.abs(z.astype(np.float64))
     assert np.all(np.abs(tcol.cpu().numpy() - exact_t) <= 1e-12 * mag)
+    # the first CGS pass is accumulated plainly in FP32 (the compensated second
+    # pass removes its error): FP32 summation accuracy, n u sum |u v|
     exact_h = U64.T @ vh.astype(np.float64)
     magh = np.abs(U64).T @ np.abs(vh.astype(np.float64))
-    assert np.all(np.abs(h1.cpu().numpy() - exact_h) <= 1e-12 * magh)
+    assert np.all(np.abs(h1.cpu().numpy() - exact_h) <= n * 2.0 ** -24 * magh)
 
 
 @pytest.mark.parametrize("withB", [False, True])
