@@ -430,3 +430,36 @@ def test_host_inputs_and_outputs(lib, h):
     lam = np.sort([4 * math.sin(i * hgrid) ** 2 + 4 * math.sin(j * hgrid) ** 2
                    for i in range(1, 5) for j in range(1, 5)])[:3]
     assert np.allclose(ev, lam, rtol=1e-9)
+
+
+# ---------------------------------------------------------------- full-size workloads
+def _reference(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "reference_runs.json")
+    return json.load(open(path))[name]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_diffusion128_matches_oracle_full_run(lib, h, precision):
+    """The 128^3 lognormal diffusion operator (n = 2,097,152) with the bench's
+    settings (p = 10, q = 40, p_hat = 15, +K = 1, Jacobi, tol 1e-8, seed 0):
+    eigenvalues against the oracle's converged full run (stored by
+    oracle/reference_runs.py) to 1e-10 relative, residuals recomputed with the
+    oracle's own matvec, B-orthonormality, and -- for the FP64 path -- the
+    oracle's cycle count."""
+    ref = _reference("diffusion128")
+    A = W.diffusion_3d(128, W.lognormal_field(128, 1.0, 1))
+    prec = lib.PRECISION_FP64 if precision == "fp64" else lib.PRECISION_MIXED
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), None, p=10, q=40, k=15, l=1, tol=1e-8, seed=0,
+                                     precision=prec)
+    assert rc == lib.OK
+    refev = np.array(ref["evals"])
+    assert np.all(np.abs(ev - refev) <= 1e-10 * np.abs(refev)), np.abs(ev - refev) / refev
+    As = A.to_scipy()
+    r = np.linalg.norm(As @ X - X * ev, axis=0) / (O.norm1(As) * np.linalg.norm(X, axis=0))
+    assert np.all(r <= 1e-8)
+    assert np.allclose(X.T @ X, np.eye(10), atol=1e-10)
+    if precision == "fp64":
+        assert info["cycles"] == ref["cycles"]
+        assert info["mv_A"] == ref["mv_A"]
