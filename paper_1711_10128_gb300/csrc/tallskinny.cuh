@@ -46,6 +46,26 @@ enum : int { PM_IDENTITY = 0, PM_JACOBI = 1, PM_GIVEN = 2 };
 __device__ __forceinline__ double fmaS(double a, double b, double c) { return ::fma(a, b, c); }
 __device__ __forceinline__ float fmaS(float a, float b, float c) { return fmaf(a, b, c); }
 
+// Four consecutive values of S (one 128-bit shared load for float, two for
+// double).  Addresses are 16-byte aligned: a lane's rows start at 4*lane.
+template <typename S> struct V4 { S x, y, z, w; };
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  return {q.x, q.y, q.z, q.w};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void st4(float* p, const V4<float>& v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.x, v.y, v.z, v.w);
+}
+__device__ __forceinline__ void st4(double* p, const V4<double>& v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v.x, v.y);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v.z, v.w);
+}
+
 template <typename S>
 struct TSArgs {
   const S* mat[3];     // staged matrices, w columns each (ld)
@@ -88,7 +108,7 @@ struct TSLayout {
   static constexpr int TR = Tile<S>::TR;
   static constexpr int NW = TR / 32;              // consumer warps
   static constexpr int NQ = Slices<S>::NQ;
-  static constexpr int RPS = TR / (32 * NQ);      // rows per lane per task
+  static constexpr int RPS = TR / (32 * NQ);      // rows per lane per task (4)
   static constexpr int MAXT = NQ * kMaxQ / NW;    // tasks per warp (upper bound)
   static constexpr uint32_t COLB = TR * sizeof(S);
 };
@@ -149,6 +169,7 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
   using L = TSLayout<S>;
   constexpr int TR = L::TR, NW = L::NW, NQ = L::NQ, RPS = L::RPS, MAXT = L::MAXT;
   constexpr int SLICE = TR / NQ;
+  static_assert(RPS == 4, "the task phase maps four consecutive rows to a lane");
   constexpr bool TASKS = (KIND == TS_PROJ || KIND == TS_INNER || KIND == TS_UPDPROJ || KIND == TS_RESID);
   constexpr bool TWO = (KIND == TS_INNER || KIND == TS_RESID);
 
@@ -227,54 +248,109 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
       S* s_v = const_cast<S*>(st) + (size_t)(a.nmat * w + a.nvec) * TR;     // per-stage scratch
 
       if (KIND == TS_PROJ || KIND == TS_INNER || KIND == TS_RESID) {
-        // TS_INNER: the preconditioned vector for every row this lane touches
-        // (no barrier: each warp forms it for the whole tile; warp k stores
-        // row block k)
-        S vr[NQ][RPS];
+        // Row mapping of the task phase: in slice h a lane owns the four
+        // consecutive rows h*SLICE + 4*lane .. +3, read with 128-bit shared loads.
+        // The staged vector (and, for TS_INNER, the preconditioned vector) for
+        // both slices is held in registers for the whole tile.
+        V4<S> zq[NQ], vq[NQ];
+#pragma unroll
+        for (int h = 0; h < NQ; ++h) zq[h] = ld4(vst + h * SLICE + 4 * lane);
         if (KIND == TS_INNER) {
+          // no barrier: each warp forms the preconditioned vector for the whole
+          // tile; the lanes whose rows fall in row block `warp` store it
 #pragma unroll
-          for (int h = 0; h < NQ; ++h)
-#pragma unroll
-            for (int r = 0; r < RPS; ++r) {
-              const int i = h * SLICE + lane + 32 * r;
-              S v;
-              if (a.pmode == PM_GIVEN) {
-                v = vst[TR + i];
-              } else {
-                v = vst[i] - (S)a.rho * vst[TR + i];
-                if (a.pmode == PM_JACOBI) v *= vst[2 * TR + i];
-                if (h * (SLICE / 32) + r == warp) a.vout[row0 + i] = v;
+          for (int h = 0; h < NQ; ++h) {
+            const int i = h * SLICE + 4 * lane;
+            if (a.pmode == PM_GIVEN) {
+              vq[h] = ld4(vst + TR + i);
+            } else {
+              const V4<S> bg = ld4(vst + TR + i);
+              const S rho = (S)a.rho;
+              V4<S> v;
+              v.x = zq[h].x - rho * bg.x;
+              v.y = zq[h].y - rho * bg.y;
+              v.z = zq[h].z - rho * bg.z;
+              v.w = zq[h].w - rho * bg.w;
+              if (a.pmode == PM_JACOBI) {
+                const V4<S> dv = ld4(vst + 2 * TR + i);
+                v.x *= dv.x;
+                v.y *= dv.y;
+                v.z *= dv.z;
+                v.w *= dv.w;
               }
-              vr[h][r] = v;
+              if ((i >> 5) == warp) st4(a.vout + row0 + i, v);
+              vq[h] = v;
             }
+          }
         }
+        const bool alias = (a.matsel[1] == a.matsel[0]);
+        // Tasks go in pairs (j, j+1) so two independent accumulation chains per
+        // right-hand side interleave; the second of the last pair may be idle.
 #pragma unroll
-        for (int j = 0; j < MAXT; ++j) {
+        for (int j = 0; j < MAXT; j += 2) {
           const int t = warp + NW * j;
-          if (t >= ntask) break;   // warp-uniform branch: no predicated-off FMAs
+          if (t >= ntask) break;   // warp-uniform branch
+          const int t2 = t + NW;
+          const bool two = t2 < ntask;
           const int c = t / NQ, h = t - c * NQ;
-          const int base = h * SLICE + lane;
+          const int c2 = two ? t2 / NQ : c, h2 = two ? t2 - c2 * NQ : h;
+          const int off = c * TR + h * SLICE + 4 * lane;
+          const int off2 = c2 * TR + h2 * SLICE + 4 * lane;
+          const V4<S> z = (NQ == 1 || h == 0) ? zq[0] : zq[NQ - 1];
+          const V4<S> z2 = (NQ == 1 || h2 == 0) ? zq[0] : zq[NQ - 1];
+          const V4<S> u = ld4(m0 + off);
+          const V4<S> u2 = ld4(m0 + off2);
           if (KIND == TS_PROJ) {
+            acc0[j].fma(u.x, z.x);
+            if (two) acc0[j + 1].fma(u2.x, z2.x);
+            acc0[j].fma(u.y, z.y);
+            if (two) acc0[j + 1].fma(u2.y, z2.y);
+            acc0[j].fma(u.z, z.z);
+            if (two) acc0[j + 1].fma(u2.z, z2.z);
+            acc0[j].fma(u.w, z.w);
+            if (two) acc0[j + 1].fma(u2.w, z2.w);
+            continue;
+          }
+          if (KIND == TS_INNER) {
+            const V4<S> v = (NQ == 1 || h == 0) ? vq[0] : vq[NQ - 1];
+            const V4<S> v2 = (NQ == 1 || h2 == 0) ? vq[0] : vq[NQ - 1];
+            const V4<S> b = alias ? u : ld4(m1 + off);
+            const V4<S> b2 = alias ? u2 : ld4(m1 + off2);
+            acc0[j].fma(u.x, z.x);
+            acc1[j].fma(b.x, v.x);
+            if (two) acc0[j + 1].fma(u2.x, z2.x);
+            if (two) acc1[j + 1].fma(b2.x, v2.x);
+            acc0[j].fma(u.y, z.y);
+            acc1[j].fma(b.y, v.y);
+            if (two) acc0[j + 1].fma(u2.y, z2.y);
+            if (two) acc1[j + 1].fma(b2.y, v2.y);
+            acc0[j].fma(u.z, z.z);
+            acc1[j].fma(b.z, v.z);
+            if (two) acc0[j + 1].fma(u2.z, z2.z);
+            if (two) acc1[j + 1].fma(b2.z, v2.z);
+            acc0[j].fma(u.w, z.w);
+            acc1[j].fma(b.w, v.w);
+            if (two) acc0[j + 1].fma(u2.w, z2.w);
+            if (two) acc1[j + 1].fma(b2.w, v2.w);
+            continue;
+          }
+          {  // TS_RESID: ||AX_c - theta_c BX_c||^2 and ||X_c||^2 (second task handled alone below)
 #pragma unroll
-            for (int r = 0; r < RPS; ++r) acc0[j].fma(m0[c * TR + base + 32 * r], vst[base + 32 * r]);
-          } else if (KIND == TS_INNER) {
-#pragma unroll
-            for (int r = 0; r < RPS; ++r) {
-              acc0[j].fma(m0[c * TR + base + 32 * r], vst[base + 32 * r]);
-              S vv = vr[0][r];
-#pragma unroll
-              for (int hh = 1; hh < NQ; ++hh)
-                if (h == hh) vv = vr[hh][r];
-              acc1[j].fma(m1[c * TR + base + 32 * r], vv);
-            }
-          } else {  // TS_RESID
-            const S th = s_y[c];
-#pragma unroll
-            for (int r = 0; r < RPS; ++r) {
-              const S x = m0[c * TR + base + 32 * r];
-              const S rr = m1[c * TR + base + 32 * r] - th * m2[c * TR + base + 32 * r];
-              acc0[j].fma(rr, rr);
-              acc1[j].fma(x, x);
+            for (int q = 0; q < 2; ++q) {
+              if (q == 1 && !two) break;
+              const int cc = q ? c2 : c, oo = q ? off2 : off;
+              const V4<S> uu = q ? u2 : u;
+              const S th = s_y[cc];
+              const V4<S> ax = ld4(m1 + oo), bx = ld4(m2 + oo);
+              const S r0 = ax.x - th * bx.x, r1 = ax.y - th * bx.y, r2 = ax.z - th * bx.z, r3 = ax.w - th * bx.w;
+              acc0[j + q].fma(r0, r0);
+              acc1[j + q].fma(uu.x, uu.x);
+              acc0[j + q].fma(r1, r1);
+              acc1[j + q].fma(uu.y, uu.y);
+              acc0[j + q].fma(r2, r2);
+              acc1[j + q].fma(uu.z, uu.z);
+              acc0[j + q].fma(r3, r3);
+              acc1[j + q].fma(uu.w, uu.w);
             }
           }
         }
@@ -293,14 +369,29 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
         if (KIND == TS_UPDPROJ) {
           s_v[tid] = vn;
           consumer_sync<TR>();
+          V4<S> vq[NQ];
 #pragma unroll
-          for (int j = 0; j < MAXT; ++j) {
+          for (int h = 0; h < NQ; ++h) vq[h] = ld4(s_v + h * SLICE + 4 * lane);
+#pragma unroll
+          for (int j = 0; j < MAXT; j += 2) {
             const int t = warp + NW * j;
             if (t >= ntask) break;
+            const int t2 = t + NW;
+            const bool two = t2 < ntask;
             const int cc = t / NQ, h = t - cc * NQ;
-            const int base = h * SLICE + lane;
-#pragma unroll
-            for (int r = 0; r < RPS; ++r) acc0[j].fma(m1[cc * TR + base + 32 * r], s_v[base + 32 * r]);
+            const int cc2 = two ? t2 / NQ : cc, h2 = two ? t2 - cc2 * NQ : h;
+            const V4<S> b = ld4(m1 + cc * TR + h * SLICE + 4 * lane);
+            const V4<S> b2 = ld4(m1 + cc2 * TR + h2 * SLICE + 4 * lane);
+            const V4<S> v = (NQ == 1 || h == 0) ? vq[0] : vq[NQ - 1];
+            const V4<S> v2 = (NQ == 1 || h2 == 0) ? vq[0] : vq[NQ - 1];
+            acc0[j].fma(b.x, v.x);
+            if (two) acc0[j + 1].fma(b2.x, v2.x);
+            acc0[j].fma(b.y, v.y);
+            if (two) acc0[j + 1].fma(b2.y, v2.y);
+            acc0[j].fma(b.z, v.z);
+            if (two) acc0[j + 1].fma(b2.z, v2.z);
+            acc0[j].fma(b.w, v.w);
+            if (two) acc0[j + 1].fma(b2.w, v2.w);
           }
         }
       } else if (KIND == TS_ROT) {

@@ -455,7 +455,17 @@ def test_full_size_diffusion128_matches_oracle_full_run(lib, h, precision):
                                      precision=prec)
     assert rc == lib.OK
     refev = np.array(ref["evals"])
-    assert np.all(np.abs(ev - refev) <= 1e-10 * np.abs(refev)), np.abs(ev - refev) / refev
+    rel = np.abs(ev - refev) / np.abs(refev)
+    if precision == "fp64":
+        # same arithmetic as the oracle up to rounding order: 1e-10 relative
+        assert np.all(rel <= 1e-10), rel
+    else:
+        # a different (FP32) trajectory: both runs stop at residual 1e-8, and the
+        # Kato-Temple bound ||r||^2 / gap of the clustered pairs 8-10 (gaps ~4e-6)
+        # is ~4e-7 absolute, so 1e-10 is not implied; the error is stated and held
+        # to 1e-8 relative
+        print("mixed path eigenvalue error vs oracle (relative):", rel)
+        assert np.all(rel <= 1e-8), rel
     As = A.to_scipy()
     r = np.linalg.norm(As @ X - X * ev, axis=0) / (O.norm1(As) * np.linalg.norm(X, axis=0))
     assert np.all(r <= 1e-8)
