@@ -1,0 +1,109 @@
+"""Pins of the FSAI oracle (oracle/fsai.py): exact inverse factors on full
+patterns, the normalisation and Kaporin-minimality of classical FSAI, the
+energy-norm identity of the loss, finite-difference gradients, known features
+and the Jacobi starting point of the MLP."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import fsai as F
+from paper_1711_10128_gb300 import workloads as W
+
+
+def test_classical_fsai_full_pattern_is_exact_inverse_factor():
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((6, 6))
+    A = X @ X.T + 6 * np.eye(6)
+    G = F.classical_fsai(sp.csr_matrix(A)).toarray()   # lower pattern = full lower triangle
+    assert np.allclose(G @ A @ G.T, np.eye(6), atol=1e-12)
+    assert np.allclose(G.T @ G, np.linalg.inv(A), atol=1e-12)
+
+
+def test_classical_fsai_diagonal_and_normalisation():
+    A = W.diffusion_3d(5, W.lognormal_field(5, 1.0, 3)).to_scipy()
+    G = F.classical_fsai(A)
+    d = np.asarray((G @ A).multiply(G).sum(axis=1)).ravel()
+    assert np.allclose(d, 1.0, atol=1e-12)          # (G A G^T)_ii = 1
+    D = sp.diags(np.arange(1.0, 9.0))
+    Gd = F.classical_fsai(D).toarray()
+    assert np.allclose(Gd, np.diag(1 / np.sqrt(np.arange(1.0, 9.0))), atol=1e-15)
+
+
+def test_classical_fsai_minimises_kaporin_on_its_pattern():
+    A = W.diffusion_3d(4, W.lognormal_field(4, 1.0, 5), axis=(1.0, 7.0, 30.0)).to_scipy()
+    G = F.classical_fsai(A)
+    k0 = F.kaporin(G, A)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        P = G.copy()
+        P.data = P.data * (1 + 1e-2 * rng.standard_normal(P.nnz))
+        assert F.kaporin(P, A) > k0 - 1e-14
+    # scaling G does not change K (it is scale invariant)
+    assert abs(F.kaporin(3.0 * G, A) - k0) < 1e-12
+
+
+def test_energy_term_equals_error_in_A_norm_minus_constant():
+    A = W.diffusion_3d(4, W.lognormal_field(4, 1.0, 6)).to_scipy()
+    Ad = A.toarray()
+    G = F.classical_fsai(A)
+    rng = np.random.default_rng(2)
+    v = rng.standard_normal(A.shape[0])
+    Mv = F.apply_M(G, v)
+    E = Mv @ (A @ Mv) - 2 * np.linalg.norm(G @ v) ** 2
+    x = np.linalg.solve(Ad, v)
+    assert abs(E - ((x - Mv) @ Ad @ (x - Mv) - v @ x)) <= 1e-10 * abs(v @ x)
+
+
+def test_loss_gradient_in_G_matches_finite_differences():
+    A = W.diffusion_3d(4, W.lognormal_field(4, 1.0, 7)).to_scipy()
+    G = F.classical_fsai(A)
+    rng = np.random.default_rng(3)
+    G.data = G.data * (1 + 0.1 * rng.standard_normal(G.nnz))
+    V = rng.standard_normal((A.shape[0], 3))
+    L, g, _ = F.loss_and_grad_G(G, A, V)
+    for e in rng.choice(G.nnz, 12, replace=False):
+        h = 1e-6 * max(1.0, abs(G.data[e]))
+        Gp, Gm = G.copy(), G.copy()
+        Gp.data[e] += h
+        Gm.data[e] -= h
+        fd = (F.loss_and_grad_G(Gp, A, V)[0] - F.loss_and_grad_G(Gm, A, V)[0]) / (2 * h)
+        assert abs(fd - g[e]) <= 1e-6 * max(1.0, abs(fd)), (e, fd, g[e])
+
+
+def test_mlp_gradient_matches_finite_differences():
+    dims = (4, 4, 4)
+    A = W.diffusion_3d(4, W.lognormal_field(4, 1.0, 8), axis=(1.0, 3.0, 9.0)).to_scipy()
+    p = F.init_mlp(4, hidden=8)
+    rng = np.random.default_rng(5)
+    p["W3"] = 0.1 * rng.standard_normal(p["W3"].shape)
+    p["b2"] = 0.1 * rng.standard_normal(p["b2"].shape)
+    V = rng.standard_normal((A.shape[0], 2))
+    L, g, _ = F.loss_and_grad_mlp(p, A, dims, V)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        flat = p[name].ravel()
+        for idx in rng.choice(flat.size, min(4, flat.size), replace=False):
+            h = 1e-6
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = F.loss_and_grad_mlp(p, A, dims, V)[0]
+            flat[idx] = old - h
+            lm = F.loss_and_grad_mlp(p, A, dims, V)[0]
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            an = g[name].ravel()[idx]
+            assert abs(fd - an) <= 1e-5 * max(1.0, abs(fd)), (name, idx, fd, an)
+    assert np.all(g["W3"][4:] == 0) and np.all(g["b3"][4:] == 0)   # unused upper outputs
+
+
+def test_features_of_constant_laplacian_and_jacobi_start():
+    N = 4
+    A = W.diffusion_3d(N).to_scipy()
+    Fe = F.features_7pt(A, (N, N, N))
+    interior = (1 * N + 1) * N + 1                     # cell (1,1,1)
+    assert np.allclose(Fe[interior], [np.log(6), -1 / 6, -1 / 6, -1 / 6, -1 / 6, -1 / 6, -1 / 6, 0.0])
+    corner = 0                                          # boundary faces add to the diagonal only
+    assert np.allclose(Fe[corner], [np.log(6), 0, -1 / 6, 0, -1 / 6, 0, -1 / 6, 0.5])
+    p = F.init_mlp(0)
+    o, _ = F.mlp_forward(p, Fe)
+    G = F.g_from_outputs(A, (N, N, N), o)
+    assert np.allclose(G.toarray(), np.diag(1 / np.sqrt(A.diagonal())), atol=1e-14)
