@@ -56,10 +56,15 @@ typedef enum {
 enum { TRPLK_F64 = 0, TRPLK_F32 = 1 };
 enum { TRPLK_SMALLEST = 0 };
 enum {
-  TRPLK_PRECOND_NONE = 0,    /* M = I                                         */
-  TRPLK_PRECOND_JACOBI = 1,  /* M = diag(A)^-1                                */
-  TRPLK_PRECOND_FSAI = 2     /* M = G^T G from a caller-supplied factor G    */
+  TRPLK_PRECOND_NONE = 0,          /* M = I                                   */
+  TRPLK_PRECOND_JACOBI = 1,        /* M = diag(A)^-1                          */
+  TRPLK_PRECOND_FSAI = 2,          /* M = G^T G, classical FSAI on tril(A)    */
+  TRPLK_PRECOND_FSAI_LEARNED = 3   /* M = G^T G, G predicted by the MLP       */
 };
+
+/* Packed MLP parameters of the learned FSAI (FP32, this order):
+ * W1[64][8], b1[64], W2[64][64], b2[64], W3[7][64], b3[7] -- 5191 floats. */
+#define TRPLK_MLP_PARAMS 5191
 enum {
   TRPLK_PRECISION_FP64 = 0,  /* FP64 storage and arithmetic throughout        */
   TRPLK_PRECISION_MIXED = 1  /* FP32 storage/SpMV, FP64-class coefficients,
@@ -92,8 +97,10 @@ typedef struct {
  *  precond    TRPLK_PRECOND_*
  *  precision  TRPLK_PRECISION_*
  *  outputs_on_device  1: evals/evecs/resid are device pointers; 0: host
- *  fsai_*     the sparse lower-triangular factor G (CSR, F64 values, same
- *             on_device as A) when precond = TRPLK_PRECOND_FSAI; M = G^T G
+ *  mlp_weights  host FP32 packed MLP parameters (TRPLK_MLP_PARAMS) for
+ *             precond = TRPLK_PRECOND_FSAI_LEARNED; grid = (nx, ny, nz) of the
+ *             7-point operator it is applied to (x fastest); mlp_bf16 = 1
+ *             runs the MLP with BF16 weights/activations (FP32 accumulation)
  *  mixed_tol  FP32-phase tolerance of the mixed path (0 = max(tol, 3e-8));
  *             the FP32 phase also stops when the target's relative residual,
  *             once below 1e-6, has not halved over 30 cycles; FP64 cycles
@@ -107,7 +114,9 @@ typedef struct {
   int precond;
   int precision;
   int outputs_on_device;
-  const trplk_csr* fsai_G;
+  const float* mlp_weights;
+  int grid[3];
+  int mlp_bf16;
   double mixed_tol;
 } trplk_params;
 
@@ -246,6 +255,60 @@ trplk_status trplk_check_residuals(trplk_handle* h, const trplk_csr* A, const tr
  * any stream capture.  No cudaMalloc, cudaFree or other allocating call. */
 trplk_status trplk_project_noalloc(int dtype, int64_t n, int64_t ld, int w, const void* BU,
                                    const void* v, double* hout, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Learned FSAI preconditioner (not in the paper: the data-parallel
+ * preconditioner of this library; the paper allows any M approximating
+ * (A - rho I)^-1, Sec. 3).  G is lower triangular on the pattern of A's lower
+ * triangle (with the diagonal, columns ascending); M = G^T G.
+ * ---------------------------------------------------------------------- */
+
+/* Number of packed MLP parameters (TRPLK_MLP_PARAMS). */
+int trplk_mlp_param_count(void);
+
+/* G's values in the order of A's lower pattern.  kind 0: classical FSAI
+ * (row i solves A[P_i, P_i] g = e_i, scaled so (G A G^T)_ii = 1; rows of at
+ * most 16 lower entries); kind 1: learned (dims = nx, ny, nz of a 7-point
+ * operator, weights = host packed MLP parameters, bf16 = precision).
+ * A: device CSR, F64.  g: device double[nnz_lower], or NULL to only return
+ * *nnz_lower.  EINVAL for a non-symmetric pattern or long rows, NOT_SPD_B if
+ * a principal block is not SPD. */
+trplk_status trplk_fsai_values(trplk_handle* h, const trplk_csr* A, int kind, const int32_t* dims,
+                               const float* weights, int bf16, double* g, int64_t* nnz_lower);
+
+/* y = G^T (G x) with G given by its values g on A's lower pattern (device,
+ * FP64, length n; y must not alias x). */
+trplk_status trplk_fsai_apply(trplk_handle* h, const trplk_csr* A, const double* g, const double* x,
+                              double* y);
+
+/* Training loss of the learned FSAI on one operator and its solver vectors
+ * V (device, FP64, n x nv column-major, ld = n): loss[0] = E + gamma K,
+ * loss[1] = E = mean_v [(Mv)^T A (Mv) - 2 ||Gv||^2] / (v^T D^-1 v),
+ * loss[2] = K = log(mean_i (G A G^T)_ii) - (2/n) sum_i log g_ii;
+ * grad: host double[TRPLK_MLP_PARAMS], d loss[0] / d weights. */
+trplk_status trplk_fsai_loss_grad(trplk_handle* h, const trplk_csr* A, const int32_t* dims,
+                                  const float* weights, int bf16, const double* V, int nv,
+                                  double gamma, double* loss, double* grad);
+
+/* Training parameters of trplk_fsai_train. */
+typedef struct {
+  int iters;            /* Adam steps (operators visited in turn)             */
+  double lr;            /* Adam learning rate                                  */
+  int vectors;          /* residual vectors harvested per operator             */
+  int harvest_cycles;   /* TRPL+K cycles (Jacobi, mixed path) per harvest      */
+  int q, k, l;          /* basis shape of the harvest solves                   */
+  uint64_t seed;        /* start-block seed of operator o is seed + o          */
+  int bf16;             /* 1: BF16 weights/activations, FP32 accumulation      */
+  double gamma;         /* weight of the Kaporin term                          */
+} trplk_train_params;
+
+/* Train the MLP: harvest solver vectors -- the residuals A x - theta x of
+ * the Ritz vectors of capped Jacobi TRPL+K runs -- on each operator (device
+ * CSR, F64, 7-point, dims 3 per operator), then `iters`
+ * Adam steps on the loss of trplk_fsai_loss_grad.  weights: host FP32 packed
+ * parameters, updated in place; losses: host double[iters] or NULL. */
+trplk_status trplk_fsai_train(trplk_handle* h, const trplk_csr* ops, const int32_t* dims, int nops,
+                              const trplk_train_params* tp, float* weights, double* losses);
 
 /* ------------------------------------------------------------------------
  * Per-kernel profiling (measurement support, not part of the method).

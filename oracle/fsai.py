@@ -18,12 +18,18 @@ F2 Classical FSAI (Kolotilina and Yeremin): g_hat_i = A[P_i, P_i]^-1 e_i,
    over G with that pattern (the pin of this module).
 F3 7-point operators on an Nx x Ny x Nz grid (x fastest): neighbour
    directions by column offset (-1, +1, -Nx, +Nx, -NxNy, +NxNy); features
-   [log a_ii, a_{-x}/a_ii, a_{+x}/a_ii, a_{-y}/a_ii, a_{+y}/a_ii,
-   a_{-z}/a_ii, a_{+z}/a_ii, (a_ii - sum_j |a_ij|)/a_ii], 0 where missing.
+   [log a_ii, c_{-x}, c_{+x}, c_{-y}, c_{+y}, c_{-z}, c_{+z},
+   (a_ii - sum_j |a_ij|)/a_ii] with the symmetrically scaled couplings
+   c_j = a_ij / sqrt(a_ii a_jj), 0 where missing.
 F4 MLP 8 -> 64 -> 64 -> 7, ReLU hidden layers; outputs map to the
    directions (-z, -y, -x, c, +x, +y, +z); g_ii = softplus(o_c)/sqrt(a_ii),
-   g_ij = o_dir/sqrt(a_ii) for the lower neighbours; the upper three outputs
-   are unused (their gradient is zero).
+   g_ij = o_dir/sqrt(a_jj) for the lower neighbours j; the upper three
+   outputs are unused (their gradient is zero).  In these variables classical
+   FSAI of a 7-point operator is a smooth function of the features
+   (o_dir = -c_dir / sqrt(1 - sum_lower c^2), softplus(o_c) =
+   1 / sqrt(1 - sum_lower c^2)), which the network can represent; row-local
+   ratios a_ij/a_ii and a 1/sqrt(a_ii) scaling could not, since classical
+   FSAI depends on the neighbours' diagonals.
 F5 Loss over solver vectors v (columns of V): the energy-norm error of Mv as
    an approximation of A^-1 v, less its G-independent part,
    E_v = (Mv)^T A (Mv) - 2 ||Gv||^2 = ||A^-1 v - Mv||_A^2 - v^T A^-1 v,
@@ -76,22 +82,18 @@ def features_7pt(A, dims):
     nx, ny, nz = dims
     n = A.shape[0]
     offs = {-1: 1, 1: 2, -nx: 3, nx: 4, -nx * ny: 5, nx * ny: 6}
+    diag = A.diagonal()
     F = np.zeros((n, 8))
     for i in range(n):
         s, e = A.indptr[i], A.indptr[i + 1]
-        aii = 0.0
+        aii = diag[i]
         off_sum = 0.0
         for jj in range(s, e):
             j, a = A.indices[jj], A.data[jj]
-            if j == i:
-                aii = a
-            else:
-                off_sum += abs(a)
-        F[i, 0] = np.log(aii)
-        for jj in range(s, e):
-            j, a = A.indices[jj], A.data[jj]
             if j != i:
-                F[i, offs[j - i]] = a / aii
+                off_sum += abs(a)
+                F[i, offs[j - i]] = a / np.sqrt(aii * diag[j])
+        F[i, 0] = np.log(aii)
         F[i, 7] = (aii - off_sum) / aii
     return F
 
@@ -139,7 +141,7 @@ def g_from_outputs(A, dims, o):
     for i in range(n):
         for jj in range(rp[i], rp[i + 1]):
             k = slot[int(cl[jj]) - i]
-            vals[jj] = (softplus(o[i, 3]) if k == 3 else o[i, k]) / np.sqrt(d[i])
+            vals[jj] = softplus(o[i, 3]) / np.sqrt(d[i]) if k == 3 else o[i, k] / np.sqrt(d[cl[jj]])
     return sp.csr_matrix((vals, cl, rp), shape=(n, n))
 
 
@@ -204,7 +206,7 @@ def loss_and_grad_mlp(p, A, dims, V):
         if k == 3:
             dO[i, 3] += gG[e] * sigmoid(o[i, 3]) / sq[i]
         else:
-            dO[i, k] += gG[e] / sq[i]
+            dO[i, k] += gG[e] / sq[j]
     # back through the MLP
     g = {}
     g["W3"] = dO.T @ h2

@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "NOT_CONVERGED
                 6: "NOT_SPD_B", 7: "NAN", 8: "ETIMEOUT"}
 F64, F32 = 0, 1
 SMALLEST = 0
-PRECOND_NONE, PRECOND_JACOBI, PRECOND_FSAI = 0, 1, 2
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_FSAI, PRECOND_FSAI_LEARNED = 0, 1, 2, 3
+MLP_PARAMS = 5191
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
 
@@ -34,8 +35,14 @@ class trplk_csr(C.Structure):
 class trplk_params(C.Structure):
     _fields_ = [("p", C.c_int), ("q", C.c_int), ("k", C.c_int), ("l", C.c_int), ("tol", C.c_double),
                 ("max_cycles", C.c_int), ("seed", C.c_uint64), ("which", C.c_int), ("precond", C.c_int),
-                ("precision", C.c_int), ("outputs_on_device", C.c_int), ("fsai_G", C.c_void_p),
-                ("mixed_tol", C.c_double)]
+                ("precision", C.c_int), ("outputs_on_device", C.c_int), ("mlp_weights", C.c_void_p),
+                ("grid", C.c_int * 3), ("mlp_bf16", C.c_int), ("mixed_tol", C.c_double)]
+
+
+class trplk_train_params(C.Structure):
+    _fields_ = [("iters", C.c_int), ("lr", C.c_double), ("vectors", C.c_int), ("harvest_cycles", C.c_int),
+                ("q", C.c_int), ("k", C.c_int), ("l", C.c_int), ("seed", C.c_uint64), ("bf16", C.c_int),
+                ("gamma", C.c_double)]
 
 
 class trplk_info(C.Structure):
@@ -75,6 +82,11 @@ def _load():
         "trplk_start_block": (st, [vp, i64, i64, i32, C.c_uint64, vp]),
         "trplk_check_residuals": (st, [vp, C.POINTER(trplk_csr), C.POINTER(trplk_csr), i64, i32, vp, vp, dbl, vp]),
         "trplk_project_noalloc": (st, [i32, i64, i64, i32, vp, vp, vp, vp]),
+        "trplk_mlp_param_count": (C.c_int, []),
+        "trplk_fsai_values": (st, [vp, C.POINTER(trplk_csr), i32, vp, vp, i32, vp, C.POINTER(C.c_int64)]),
+        "trplk_fsai_apply": (st, [vp, C.POINTER(trplk_csr), vp, vp, vp]),
+        "trplk_fsai_loss_grad": (st, [vp, C.POINTER(trplk_csr), vp, vp, i32, vp, i32, dbl, vp, vp]),
+        "trplk_fsai_train": (st, [vp, C.POINTER(trplk_csr), vp, i32, C.POINTER(trplk_train_params), vp, vp]),
         "trplk_profile": (st, [vp, i32]),
         "trplk_profile_read": (st, [vp, i32, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "trplk_profile_kind_name": (C.c_char_p, [i32]),
@@ -221,6 +233,49 @@ def trplk_project_noalloc(dtype, n, ld, w, BU, v, hout, stream=None):
     return rc
 
 
+def trplk_fsai_values(h, A, kind, dims=None, weights=None, bf16=0, g=None):
+    """G values on A's lower pattern (device tensor g) -> nnz of the pattern."""
+    nnz = C.c_int64()
+    d = (C.c_int32 * 3)(*dims) if dims is not None else None
+    h.check(LIB.trplk_fsai_values(h.h, C.byref(A), kind, d, ptr(weights), int(bf16), ptr(g), C.byref(nnz)))
+    return nnz.value
+
+
+def trplk_fsai_apply(h, A, g, x, y):
+    return h.check(LIB.trplk_fsai_apply(h.h, C.byref(A), ptr(g), ptr(x), ptr(y)))
+
+
+def trplk_fsai_loss_grad(h, A, dims, weights, bf16, V, nv, gamma=0.1):
+    """(loss[3], grad[MLP_PARAMS]) as numpy arrays."""
+    loss = np.zeros(3)
+    grad = np.zeros(MLP_PARAMS)
+    d = (C.c_int32 * 3)(*dims)
+    h.check(LIB.trplk_fsai_loss_grad(h.h, C.byref(A), d, ptr(weights), int(bf16), ptr(V), int(nv), float(gamma),
+                                     ptr(loss), ptr(grad)))
+    return loss, grad
+
+
+def trplk_fsai_train(h, ops, dims, tp, weights, iters=None):
+    """Train in place: ops list of device trplk_csr, dims list of (nx, ny, nz),
+    weights float32 numpy array (MLP_PARAMS); returns the loss history."""
+    arr = (trplk_csr * len(ops))(*ops)
+    d = (C.c_int32 * (3 * len(ops)))(*[int(x) for t in dims for x in t])
+    losses = np.zeros(max(tp.iters, 1))
+    h.check(LIB.trplk_fsai_train(h.h, arr, d, len(ops), C.byref(tp), ptr(weights), ptr(losses)))
+    return losses[:tp.iters]
+
+
+def pack_mlp(p):
+    """Pack a dict of MLP arrays (W1, b1, W2, b2, W3, b3) into the FP32 layout."""
+    return np.concatenate([np.asarray(p[k], np.float32).ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+
+def unpack_mlp(w):
+    w = np.asarray(w, np.float64)
+    return dict(W1=w[0:512].reshape(64, 8), b1=w[512:576], W2=w[576:4672].reshape(64, 64), b2=w[4672:4736],
+                W3=w[4736:5184].reshape(7, 64), b3=w[5184:5191])
+
+
 def trplk_profile(h, enable):
     return h.check(LIB.trplk_profile(h.h, int(enable)))
 
@@ -254,20 +309,25 @@ def profile_summary(h):
 
 # ---------------------------------------------------------------- convenience
 def make_params(p, q, k, l, tol=1e-8, max_cycles=5000, seed=0, precond=PRECOND_JACOBI,
-                precision=PRECISION_FP64, outputs_on_device=0, mixed_tol=0.0):
-    return trplk_params(p, q, k, l, tol, max_cycles, seed, SMALLEST, precond, precision, outputs_on_device, None,
-                        mixed_tol)
+                precision=PRECISION_FP64, outputs_on_device=0, mixed_tol=0.0, mlp_weights=None, grid=(0, 0, 0),
+                mlp_bf16=1):
+    prm = trplk_params(p, q, k, l, tol, max_cycles, seed, SMALLEST, precond, precision, outputs_on_device,
+                       ptr(mlp_weights), (C.c_int * 3)(*grid), int(mlp_bf16), mixed_tol)
+    prm._keep = mlp_weights
+    return prm
 
 
 def solve(h: Handle, A: trplk_csr, B=None, *, p, q, k, l, tol=1e-8, X0=None, max_cycles=5000, seed=0,
-          precond=PRECOND_JACOBI, precision=PRECISION_FP64, mixed_tol=0.0):
+          precond=PRECOND_JACOBI, precision=PRECISION_FP64, mixed_tol=0.0, mlp_weights=None, grid=(0, 0, 0),
+          mlp_bf16=1):
     """Solve with host outputs (numpy); returns (evals, evecs, resid, status, info dict)."""
     n = A.n
     evals = np.zeros(p)
     evecs = np.zeros((p, n))       # column-major n x p == row-major p x n
     resid = np.zeros(p)
     info = trplk_info()
-    params = make_params(p, q, k, l, tol, max_cycles, seed, precond, precision, 0, mixed_tol)
+    params = make_params(p, q, k, l, tol, max_cycles, seed, precond, precision, 0, mixed_tol, mlp_weights, grid,
+                         mlp_bf16)
     X0c = None
     if X0 is not None:
         X0c = X0 if _is_device(X0) else np.ascontiguousarray(np.asarray(X0, np.float64).T)

@@ -20,61 +20,40 @@
 
 using namespace trplk;
 
-// ---------------------------------------------------------------- handle
-struct trplk_handle {
-  Ctx ctx;
-  Profiler prof;
-  bool own_stream = false;
-  std::string err;
-  struct Buf {
-    void* p = nullptr;
-    size_t bytes = 0;
-  };
-  std::map<std::string, Buf> bufs;
-  std::map<std::string, std::string> layouts;   // workspace group -> layout key
-  double* pinned = nullptr;   // host read-back area
-  size_t pinned_bytes = 0;
+#include "handle.h"
 
-  // A named device buffer of at least `bytes`, zero-filled when (re)allocated
-  // or when `zero` is set.
-  void* get(const std::string& name, size_t bytes, bool zero = false) {
-    bytes = std::max<size_t>(bytes, 256);
-    Buf& b = bufs[name];
-    if (b.bytes < bytes) {
-      if (b.p) cudaFree(b.p);
-      b.p = nullptr;
-      b.bytes = 0;
-      cudaError_t e = cudaMalloc(&b.p, bytes);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        throw Error(TRPLK_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes for " + name + " failed");
-      }
-      b.bytes = bytes;
-      TRPLK_CUDA_TRY(cudaMemsetAsync(b.p, 0, bytes, ctx.stream));
-    } else if (zero) {
-      TRPLK_CUDA_TRY(cudaMemsetAsync(b.p, 0, bytes, ctx.stream));
-    }
-    return b.p;
+// Build the SELL-32 copy of a device CSR (values from the FP64 array; an
+// FP32 copy too when f32 != nullptr) unless padding would add more than 25%.
+void attach_sell(trplk_handle* h, DevCsr<double>& d, const std::string& tag, DevCsr<float>* f32) {
+  const Ctx& c = h->ctx;
+  const int64_t nslices = (d.n + 31) / 32;
+  auto* lens = static_cast<int32_t*>(h->get(tag + ".sl_len", nslices * sizeof(int32_t)));
+  sell_lengths(c, d.n, d.rowptr, lens);
+  std::vector<int32_t> hl(nslices);
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(hl.data(), lens, nslices * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  h->sync();
+  std::vector<int64_t> ptr(nslices + 1, 0);
+  for (int64_t s = 0; s < nslices; ++s) ptr[s + 1] = ptr[s] + 32 * (int64_t)hl[s];
+  const int64_t padded = ptr[nslices];
+  if ((double)padded > 1.25 * (double)d.nnz + 32.0 * nslices) return;
+  auto* sp = static_cast<int64_t*>(h->get(tag + ".sl_ptr", (nslices + 1) * sizeof(int64_t)));
+  auto* sc = static_cast<int32_t*>(h->get(tag + ".sl_col", padded * sizeof(int32_t)));
+  auto* sv = static_cast<double*>(h->get(tag + ".sl_val", padded * sizeof(double)));
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(sp, ptr.data(), (nslices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
+  sell_fill<double>(c, d.n, d.rowptr, d.col, d.val, sp, sc, sv);
+  d.sl_ptr = sp;
+  d.sl_col = sc;
+  d.sl_val = sv;
+  if (f32) {
+    auto* svf = static_cast<float*>(h->get(tag + ".sl_valf", padded * sizeof(float)));
+    sell_fill<float>(c, d.n, d.rowptr, d.col, d.val, sp, nullptr, svf);
+    f32->sl_ptr = sp;
+    f32->sl_col = sc;
+    f32->sl_val = svf;
   }
-  double* host(size_t count) {
-    size_t bytes = count * sizeof(double);
-    if (pinned_bytes < bytes) {
-      if (pinned) cudaFreeHost(pinned);
-      pinned = nullptr;
-      TRPLK_CUDA_TRY(cudaMallocHost(&pinned, bytes));
-      pinned_bytes = bytes;
-    }
-    return pinned;
-  }
-  void sync() { TRPLK_CUDA_TRY(cudaStreamSynchronize(ctx.stream)); }
-  int read_status() {
-    int s = 0;
-    TRPLK_CUDA_TRY(cudaMemcpyAsync(&s, ctx.status, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
-    sync();
-    return s;
-  }
-  void clear_status() { TRPLK_CUDA_TRY(cudaMemsetAsync(ctx.status, 0, sizeof(int), ctx.stream)); }
-};
+  h->sync();   // ptr (host vector) must stay alive until its copy finished
+}
+
 
 namespace {
 
@@ -143,38 +122,6 @@ __global__ void set_diag_block_kernel(double* T, int ldT, int k, const double* t
     const int j = e / k, i = e - j * k;
     T[(int64_t)j * ldT + i] = (i == j) ? theta[i] : 0.0;
   }
-}
-
-// Build the SELL-32 copy of a device CSR (values from the FP64 array; an
-// FP32 copy too when f32 != nullptr) unless padding would add more than 25%.
-void attach_sell(trplk_handle* h, DevCsr<double>& d, const std::string& tag, DevCsr<float>* f32) {
-  const Ctx& c = h->ctx;
-  const int64_t nslices = (d.n + 31) / 32;
-  auto* lens = static_cast<int32_t*>(h->get(tag + ".sl_len", nslices * sizeof(int32_t)));
-  sell_lengths(c, d.n, d.rowptr, lens);
-  std::vector<int32_t> hl(nslices);
-  TRPLK_CUDA_TRY(cudaMemcpyAsync(hl.data(), lens, nslices * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
-  h->sync();
-  std::vector<int64_t> ptr(nslices + 1, 0);
-  for (int64_t s = 0; s < nslices; ++s) ptr[s + 1] = ptr[s] + 32 * (int64_t)hl[s];
-  const int64_t padded = ptr[nslices];
-  if ((double)padded > 1.25 * (double)d.nnz + 32.0 * nslices) return;
-  auto* sp = static_cast<int64_t*>(h->get(tag + ".sl_ptr", (nslices + 1) * sizeof(int64_t)));
-  auto* sc = static_cast<int32_t*>(h->get(tag + ".sl_col", padded * sizeof(int32_t)));
-  auto* sv = static_cast<double*>(h->get(tag + ".sl_val", padded * sizeof(double)));
-  TRPLK_CUDA_TRY(cudaMemcpyAsync(sp, ptr.data(), (nslices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
-  sell_fill<double>(c, d.n, d.rowptr, d.col, d.val, sp, sc, sv);
-  d.sl_ptr = sp;
-  d.sl_col = sc;
-  d.sl_val = sv;
-  if (f32) {
-    auto* svf = static_cast<float*>(h->get(tag + ".sl_valf", padded * sizeof(float)));
-    sell_fill<float>(c, d.n, d.rowptr, d.col, d.val, sp, nullptr, svf);
-    f32->sl_ptr = sp;
-    f32->sl_col = sc;
-    f32->sl_val = svf;
-  }
-  h->sync();   // ptr (host vector) must stay alive until its copy finished
 }
 
 // Upload or wrap a caller's CSR; `tag` names the workspace slots.
@@ -266,6 +213,10 @@ struct Solver {
   const DevCsr<S>* B;
   const S* dinv;
   int pmode;
+  const DevCsr<S>* MG = nullptr;    // FSAI factor G (M = G^T G) when set
+  const DevCsr<S>* MGT = nullptr;
+  S* rtmp = nullptr;
+  S* ttmp = nullptr;
   double normA;
   double eps_breakdown;
   // workspace
@@ -307,10 +258,18 @@ struct Solver {
     scale = static_cast<double*>(h->get(tag + ".scale", 8 * sizeof(double)));
     rn = static_cast<double*>(h->get(tag + ".rn", kMaxQ * sizeof(double)));
     tmp64 = static_cast<double*>(h->get(tag + ".tmp64", ld * sizeof(double), fresh));
+    rtmp = static_cast<S*>(h->get(tag + ".rtmp", ld * sizeof(S), fresh));
+    ttmp = static_cast<S*>(h->get(tag + ".ttmp", ld * sizeof(S), fresh));
     xn = static_cast<double*>(h->get(tag + ".xn", kMaxQ * sizeof(double)));
   }
 
   S* col(S* M, int j) { return M + (size_t)j * ld; }
+
+  // out = G^T (G in) (FSAI), two sparse matvecs
+  void apply_fsai(const S* in, S* out) {
+    spmv<S>(c, *MG, in, ttmp);
+    spmv<S>(c, *MGT, ttmp, out);
+  }
 
   // v <- CGS2(v) against the w columns of (U, BU) given h1 = BU^T v; leaves
   // v unnormalised, bv = B v, betas[slot] = (beta, beta0), *scale = 1/beta.
@@ -434,7 +393,12 @@ struct Solver {
       }
       check_launch("set_diag_block");
       // first Lanczos vector u = M (A x_t - rho B x_t)  (Algorithm 1, restart)
-      restart_vector<S>(c, ld, col(AU[cur], t), col(BU[cur], t), theta + t, dinv, pmode, v);
+      if (MG) {
+        restart_vector<S>(c, ld, col(AU[cur], t), col(BU[cur], t), theta + t, nullptr, PM_IDENTITY, rtmp);
+        apply_fsai(rtmp, v);
+      } else {
+        restart_vector<S>(c, ld, col(AU[cur], t), col(BU[cur], t), theta + t, dinv, pmode, v);
+      }
       out.prec++;
       ts_project<S>(c, ld, k, BU[cur], v, h1);
       orthonormalize_tail(cur, k, 0, out);
@@ -446,8 +410,15 @@ struct Solver {
         append(cur, w, out);
         ++w;
         if (j < m - 1) {
-          ts_inner<S>(c, ld, w, U[cur], BU[cur], col(AU[cur], w - 1), col(BU[cur], w - 1), dinv, pmode, rho, v,
-                      T + (size_t)(w - 1) * ldT, h1);
+          if (MG) {   // M = G^T G, then the fused pass with the preconditioned vector given
+            axpby_shift<S>(c, ld, col(AU[cur], w - 1), col(BU[cur], w - 1), rho, rtmp);
+            apply_fsai(rtmp, v);
+            ts_inner<S>(c, ld, w, U[cur], BU[cur], col(AU[cur], w - 1), col(BU[cur], w - 1), nullptr, PM_GIVEN, rho,
+                        v, T + (size_t)(w - 1) * ldT, h1);
+          } else {
+            ts_inner<S>(c, ld, w, U[cur], BU[cur], col(AU[cur], w - 1), col(BU[cur], w - 1), dinv, pmode, rho, v,
+                        T + (size_t)(w - 1) * ldT, h1);
+          }
           out.prec++;
           orthonormalize_tail(cur, w, j + 1, out);
         } else {
@@ -567,27 +538,12 @@ void validate_params(const trplk_params* P, int64_t n) {
   if (P->q > n) throw Error(TRPLK_EINVAL, "q must be <= n");
   if (!(P->tol > 0.0)) throw Error(TRPLK_EINVAL, "tol must be > 0");
   if (P->max_cycles < 1) throw Error(TRPLK_EINVAL, "max_cycles must be >= 1");
-  if (P->precond < TRPLK_PRECOND_NONE || P->precond > TRPLK_PRECOND_JACOBI)
+  if (P->precond < TRPLK_PRECOND_NONE || P->precond > TRPLK_PRECOND_FSAI_LEARNED)
     throw Error(TRPLK_EINVAL, "unsupported preconditioner");
+  if (P->precond == TRPLK_PRECOND_FSAI_LEARNED && !P->mlp_weights)
+    throw Error(TRPLK_EINVAL, "learned FSAI needs mlp_weights");
   if (P->precision != TRPLK_PRECISION_FP64 && P->precision != TRPLK_PRECISION_MIXED)
     throw Error(TRPLK_EINVAL, "unknown precision");
-}
-
-template <typename F>
-trplk_status guarded(trplk_handle* h, F&& f) {
-  if (!h) return TRPLK_EINVAL;
-  h->err.clear();
-  try {
-    TRPLK_CUDA_TRY(cudaSetDevice(h->ctx.device));
-    return f();
-  } catch (const Error& e) {
-    h->err = e.msg;
-    if (e.code == TRPLK_ECUDA) cudaGetLastError();
-    return e.code;
-  } catch (const std::exception& e) {
-    h->err = e.what();
-    return TRPLK_ECUDA;
-  }
 }
 
 DevCsr<double> dev_csr64(const trplk_csr* M) {
@@ -680,6 +636,10 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
         convert<float, double>(c, ld, dinv64, dinv32);
       }
     }
+    FsaiPrecond fsai;
+    if (P->precond == TRPLK_PRECOND_FSAI || P->precond == TRPLK_PRECOND_FSAI_LEARNED)
+      fsai = build_fsai_precond(h, Aop.d, P->precond == TRPLK_PRECOND_FSAI ? 0 : 1, P->grid, P->mlp_weights,
+                                P->mlp_bf16 != 0, mixed);
     // start block (double, ld)
     double* X0d = static_cast<double*>(h->get("X0", (size_t)ld * P->k * sizeof(double), X0 != nullptr));
     if (X0) {
@@ -697,6 +657,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
     bool breakdown = false;
     if (!mixed) {
       Solver<double> S(h, "f64", n, P->p, P->q, P->k, P->l, P->tol, P->max_cycles, Aop, Bop, hasB, dinv64, pmode);
+      if (fsai.ok) { S.MG = &fsai.G; S.MGT = &fsai.GT; }
       res = S.run(X0d);
       inf.cycles = res.cycles;
       inf.mv_A = res.mvA;
@@ -713,6 +674,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
       Solver<float> S32(h, "f32", n, P->p, P->q, P->k, P->l, std::max(tol32, P->tol), P->max_cycles, Aop, Bop, hasB,
                         dinv32, pmode);
       S32.stall_window = 30;
+      if (fsai.ok) { S32.MG = &fsai.Gf; S32.MGT = &fsai.GTf; }
       SolveOut r32 = S32.run(X0d);
       // promote the k Ritz vectors and refine in FP64 from them
       double* Xr = static_cast<double*>(h->get("Xrefine", (size_t)ld * P->k * sizeof(double)));
@@ -721,6 +683,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
                          Bop, hasB, dinv64, pmode);
       S64.skip_converged = true;
       S64.check_start = true;
+      if (fsai.ok) { S64.MG = &fsai.G; S64.MGT = &fsai.GT; }
       SolveOut r64 = S64.run(Xr);
       inf.cycles = r32.cycles;
       inf.refine_cycles = r64.cycles;

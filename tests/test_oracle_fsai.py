@@ -103,7 +103,28 @@ def test_features_of_constant_laplacian_and_jacobi_start():
     assert np.allclose(Fe[interior], [np.log(6), -1 / 6, -1 / 6, -1 / 6, -1 / 6, -1 / 6, -1 / 6, 0.0])
     corner = 0                                          # boundary faces add to the diagonal only
     assert np.allclose(Fe[corner], [np.log(6), 0, -1 / 6, 0, -1 / 6, 0, -1 / 6, 0.5])
+    # scaled couplings use both diagonals: a_ij / sqrt(a_ii a_jj)
+    B = W.diffusion_3d(N, W.lognormal_field(N, 1.0, 2)).to_scipy()
+    Fb = F.features_7pt(B, (N, N, N))
+    i = interior
+    assert np.isclose(Fb[i, 1], B[i, i - 1] / np.sqrt(B[i, i] * B[i - 1, i - 1]))
     p = F.init_mlp(0)
     o, _ = F.mlp_forward(p, Fe)
     G = F.g_from_outputs(A, (N, N, N), o)
     assert np.allclose(G.toarray(), np.diag(1 / np.sqrt(A.diagonal())), atol=1e-14)
+
+
+def test_classical_fsai_is_representable_by_the_output_map():
+    """With the scaled couplings of F3 and the 1/sqrt(a_jj) scaling of F4,
+    classical FSAI of a 7-point operator is o_dir = -c_dir / sqrt(1 - s),
+    softplus(o_c) = 1 / sqrt(1 - s), s = sum of the squared lower couplings."""
+    N = 5
+    A = W.anisotropic_diffusion(N, 1003).to_scipy()
+    Fe = F.features_7pt(A, (N, N, N))
+    c = Fe[:, [5, 3, 1]]                      # lower couplings (-z, -y, -x)
+    s = (c ** 2).sum(axis=1)
+    o = np.zeros((A.shape[0], 7))
+    o[:, 0:3] = -c / np.sqrt(1 - s)[:, None]
+    o[:, 3] = np.log(np.expm1(1 / np.sqrt(1 - s)))
+    G = F.g_from_outputs(A, (N, N, N), o)
+    assert np.allclose(G.toarray(), F.classical_fsai(A).toarray(), atol=1e-12)
