@@ -16,6 +16,14 @@ mixed solve end to end from pinned host memory (`e2e`), the roofline of the
 dominant kernel family measured with CUDA events inside the timed region,
 the SpMV bandwidth, and the CPU oracle on a bounded sample (`cpu_baseline`).
 
+`--workload` selects another operator class (the default is the one above):
+q1pencil96 (trilinear Q1 stiffness/mass pencil on 96^3 elements, 20
+smallest, q = 50, p_hat = 25), chunglu22 (L + 1e-3 I of a 2^22-vertex
+Chung-Lu graph's largest component, 16 smallest, q = 40, p_hat = 20),
+aniso128 (anisotropic 128^3 diffusion, 20 smallest, q = 50, p_hat = 25, with
+the learned FSAI preconditioner trained first on twelve 32^3 operators of the
+family, compared against Jacobi and classical FSAI in both precisions).
+
 `--impl reference` times the CPU oracle (FP64 numpy/scipy) instead.
 Multi-GPU: one process per GPU (torchrun); the path does not shard, so each
 rank runs an independent replica; the slowest rank's time is reported.
@@ -35,8 +43,23 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="diffusion3d_128_lognormal", N=128, sigma=1.0, coef_seed=1, p=10, q=40, k=15, l=1, tol=1e-8,
-                seed=0)
+WORKLOADS = {
+    # the default: 3D 7-point lognormal(0, 1) diffusion on 128^3, Jacobi
+    "diffusion128": dict(name="diffusion3d_128_lognormal", N=128, sigma=1.0, coef_seed=1, p=10, q=40, k=15, l=1,
+                         tol=1e-8, seed=0, precond="jacobi"),
+    # trilinear Q1 stiffness/mass pencil on 96^3 elements, E ~ U[1, 10] (seed 2), Jacobi on A
+    "q1pencil96": dict(name="q1_fem_pencil_96", N=96, E_seed=2, p=20, q=50, k=25, l=1, tol=1e-8, seed=0,
+                       precond="jacobi"),
+    # L + 1e-3 I of a Chung-Lu graph, 2^22 vertices, mean degree 16, gamma 2.1 (seed 3), largest component
+    "chunglu22": dict(name="chung_lu_laplacian_2^22_lcc", n=1 << 22, mean=16.0, gamma=2.1, graph_seed=3, p=16, q=40,
+                      k=20, l=1, tol=1e-8, seed=0, precond="jacobi"),
+    # anisotropic 7-point diffusion on 128^3 (held-out operator, seed 2000): learned FSAI trained on
+    # twelve 32^3 operators of the same family (seeds 1000-1011), against Jacobi and classical FSAI
+    "aniso128": dict(name="anisotropic_diffusion_128_learned_fsai", N=128, op_seed=2000, train_N=32,
+                     train_seeds=list(range(1000, 1012)), p=20, q=50, k=25, l=1, tol=1e-8, seed=0,
+                     precond="fsai_learned"),
+}
+WORKLOAD = dict(WORKLOADS["diffusion128"], key="diffusion128")
 METRIC = "s to p eigpairs @resid 1e-8, learned/FP32 vs plain FP64; SpMV HBM GB/s"
 
 
@@ -49,19 +72,36 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solves")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--workload", default="diffusion128", choices=sorted(WORKLOADS),
+                    help="diffusion128 is the headline; the others measure the remaining operator classes")
+    args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = dict(WORKLOADS[args.workload], key=args.workload)
+    return args
 
 
 def build_workload():
+    """(A, B or None) of the selected workload."""
+    import numpy as np
     from paper_1711_10128_gb300 import workloads as W
-    A = W.diffusion_3d(WORKLOAD["N"], W.lognormal_field(WORKLOAD["N"], WORKLOAD["sigma"], WORKLOAD["coef_seed"]))
-    return A
+    w = WORKLOAD
+    if "sigma" in w:
+        return W.diffusion_3d(w["N"], W.lognormal_field(w["N"], w["sigma"], w["coef_seed"])), None
+    if "E_seed" in w:
+        N = w["N"]
+        return W.fem_q1_pencil(N, np.random.default_rng(w["E_seed"]).uniform(1.0, 10.0, (N, N, N)))
+    if "graph_seed" in w:
+        return W.chung_lu_laplacian(w["n"], w["mean"], w["gamma"], w["graph_seed"]), None
+    return W.anisotropic_diffusion(w["N"], w["op_seed"]), None
 
 
-def config_dict(A, path):
-    return {"workload": WORKLOAD["name"], "n": A.n, "nnz": A.nnz, "p": WORKLOAD["p"], "q": WORKLOAD["q"],
-            "k": WORKLOAD["k"], "l": WORKLOAD["l"], "tol": WORKLOAD["tol"], "precond": "jacobi", "path": path,
-            "l2": "inputs larger than L2 (basis 0.3-0.7 GB per copy; matrix 0.17 GB)"}
+def config_dict(A, B, path):
+    d = {"workload": WORKLOAD["name"], "n": A.n, "nnz": A.nnz, "p": WORKLOAD["p"], "q": WORKLOAD["q"],
+         "k": WORKLOAD["k"], "l": WORKLOAD["l"], "tol": WORKLOAD["tol"], "precond": WORKLOAD["precond"],
+         "path": path, "l2": "inputs larger than L2 (every basis copy and the matrix exceed 129 MB)"}
+    if B is not None:
+        d["nnz_B"] = B.nnz
+    return d
 
 
 # ---------------------------------------------------------------- clocks
@@ -172,15 +212,19 @@ def traffic_for(kernel_family):
 
 
 # ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(A):
+def oracle_sample(A, B, cycles_hint=None):
     """Time the FP64 oracle on init + 1 and init + 2 cycles of the same solve
     and extrapolate to a whole solve with the oracle's own cycle count for this
-    workload (stored by oracle/reference_runs.py); returns (seconds, sample text)."""
+    workload (stored by oracle/reference_runs.py; else `cycles_hint`, the GPU
+    FP64 path's count); returns (seconds, sample text).  The oracle runs with
+    Jacobi (its only built-in preconditioner) on every workload."""
     from oracle import trplk as O
     from paper_1711_10128_gb300 import workloads as W
+    w = WORKLOAD
     As = A.to_scipy()
-    X0 = W.start_block(A.n, WORKLOAD["k"], WORKLOAD["seed"])
-    args = (As, None, WORKLOAD["p"], WORKLOAD["q"], WORKLOAD["k"], WORKLOAD["l"], WORKLOAD["tol"], X0, "jacobi")
+    Bs = None if B is None else B.to_scipy()
+    X0 = W.start_block(A.n, w["k"], w["seed"])
+    args = (As, Bs, w["p"], w["q"], w["k"], w["l"], w["tol"], X0, "jacobi")
     t0 = time.perf_counter()
     O.solve(*args, max_cycles=1)
     t1 = time.perf_counter() - t0
@@ -192,13 +236,15 @@ def oracle_sample(A):
     ref = os.path.join(ROOT, "oracle", "reference_runs.json")
     cycles, src = None, None
     if os.path.exists(ref):
-        d = json.load(open(ref)).get("diffusion128")
-        if d:
+        d = json.load(open(ref)).get(w["key"])
+        if d and d.get("status") == "ok":
             cycles, src = d["cycles"], "oracle full run"
+    if cycles is None and cycles_hint:
+        cycles, src = cycles_hint, "cycle count of the FP64 GPU solve"
     if cycles is None:
-        cycles, src = 125, "cycle count of the FP64 GPU solve"
+        cycles, src = 2, "no full-run cycle count known: init + 2 cycles only"
     secs = init + per_cycle * cycles
-    text = (f"oracle init + 1 and + 2 cycles timed ({t1:.1f} s, {t2:.1f} s): init {init:.1f} s, "
+    text = (f"oracle (FP64, Jacobi) init + 1 and + 2 cycles timed ({t1:.1f} s, {t2:.1f} s): init {init:.1f} s, "
             f"{per_cycle:.1f} s/cycle, extrapolated to {cycles} cycles ({src})")
     return secs, text
 
@@ -206,11 +252,11 @@ def oracle_sample(A):
 def run_reference(args, world, rank, pg):
     if rank != 0:
         return 0
-    A = build_workload()
+    A, B = build_workload()
     vals = []
     sample = ""
     for i in range(args.warmup + args.steps):
-        secs, sample = oracle_sample(A) if i >= args.warmup or i == 0 else (None, sample)
+        secs, sample = oracle_sample(A, B) if i >= args.warmup or i == 0 else (None, sample)
         if i >= args.warmup:
             vals.append(secs)
     value = statistics.mean(vals)
@@ -218,7 +264,7 @@ def run_reference(args, world, rank, pg):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(A, "cpu oracle fp64"),
+            "config": config_dict(A, B, "cpu oracle fp64 (jacobi)"),
             "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -226,6 +272,33 @@ def run_reference(args, world, rank, pg):
 
 
 # ---------------------------------------------------------------- our path
+def train_learned_fsai(lib, h, dev):
+    """Train the learned-FSAI MLP on the training operators of the workload;
+    returns (weights, seconds, first and last mean loss)."""
+    import torch
+    from paper_1711_10128_gb300 import workloads as W
+    w = WORKLOAD
+    N = w["train_N"]
+    ops = []
+    for s in w["train_seeds"]:
+        T = W.anisotropic_diffusion(N, s)
+        ops.append(lib.make_csr(torch.from_numpy(T.rowptr).to(dev), torch.from_numpy(T.col).to(dev),
+                                torch.from_numpy(T.val).to(dev)))
+    weights = lib.trplk_fsai_mlp_init(0)
+    tp = lib.trplk_train_params(iters=20 * len(ops), lr=2e-3, vectors=8, harvest_cycles=6, q=24, k=10, l=1, seed=5,
+                                bf16=1, gamma=0.1)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    losses = lib.trplk_fsai_train(h, ops, [(N, N, N)] * len(ops), tp, weights)
+    torch.cuda.synchronize(dev)
+    secs = time.perf_counter() - t0
+    m = len(ops)
+    return weights, secs, float(losses[:m].mean()), float(losses[-m:].mean())
+
+
+PRECONDS = {"jacobi": "PRECOND_JACOBI", "fsai": "PRECOND_FSAI", "fsai_learned": "PRECOND_FSAI_LEARNED"}
+
+
 def run_ours(args, world, rank, local, pg):
     import numpy as np
     import torch
@@ -235,29 +308,48 @@ def run_ours(args, world, rank, local, pg):
     __graft_entry__.build()
     from paper_1711_10128_gb300 import binding as lib
 
-    A = build_workload()
+    A, B = build_workload()
     dev = f"cuda:{local}"
     stream = torch.cuda.Stream(device=dev)
     h = lib.Handle(local, stream.cuda_stream)
-    rp, cl, vl = (torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.col).to(dev),
-                  torch.from_numpy(A.val).to(dev))
-    Ad = lib.make_csr(rp, cl, vl)
+
+    def to_dev(M):
+        if M is None:
+            return None, None
+        t = (torch.from_numpy(M.rowptr).to(dev), torch.from_numpy(M.col).to(dev), torch.from_numpy(M.val).to(dev))
+        return lib.make_csr(*t), t
+
+    Ad, _keepA = to_dev(A)
+    Bd, _keepB = to_dev(B)
     P = WORKLOAD
     n, p = A.n, P["p"]
     ev_d = torch.zeros(p, dtype=torch.float64, device=dev)
     X_d = torch.zeros((p, n), dtype=torch.float64, device=dev)
     r_d = torch.zeros(p, dtype=torch.float64, device=dev)
 
-    def solve_device(precision):
+    setup = {}
+    weights, grid = None, (0, 0, 0)
+    if P["precond"] == "fsai_learned":
+        weights, tsec, l0, l1 = train_learned_fsai(lib, h, dev)
+        grid = (P["N"],) * 3
+        setup = {"train_seconds": tsec, "train_ops": len(P["train_seeds"]), "train_grid": P["train_N"],
+                 "train_loss_first": l0, "train_loss_last": l1,
+                 "note": "training is a one-off offline cost, outside every timed solve; the G build "
+                         "(features, MLP, pattern) runs inside each timed solve"}
+
+    def params(precision, precond, on_device):
+        return lib.make_params(P["p"], P["q"], P["k"], P["l"], P["tol"], 5000, P["seed"],
+                               getattr(lib, PRECONDS[precond]), precision, on_device, 0.0,
+                               weights if precond == "fsai_learned" else None, grid, 1)
+
+    def solve_device(precision, precond):
         info = lib.trplk_info()
-        params = lib.make_params(P["p"], P["q"], P["k"], P["l"], P["tol"], 5000, P["seed"], lib.PRECOND_JACOBI,
-                                 precision, 1)
-        rc = lib.trplk_solve(h, Ad, None, params, None, ev_d, X_d, r_d, info)
+        rc = lib.trplk_solve(h, Ad, Bd, params(precision, precond, 1), None, ev_d, X_d, r_d, info)
         return rc, info.as_dict()
 
-    def timed(precision, steps, warmup, profile=False):
+    def timed(precision, precond, steps, warmup, profile=False):
         for _ in range(warmup):
-            solve_device(precision)
+            solve_device(precision, precond)
         torch.cuda.synchronize(dev)
         barrier(pg, local)
         sampler = ClockSampler(local)
@@ -269,7 +361,7 @@ def run_ours(args, world, rank, local, pg):
         infos = []
         e0.record(stream)
         for _ in range(steps):
-            rc, info = solve_device(precision)
+            rc, info = solve_device(precision, precond)
             if rc != lib.OK:
                 raise RuntimeError(f"solve did not converge: {info}")
             infos.append(info)
@@ -285,15 +377,18 @@ def run_ours(args, world, rank, local, pg):
         return ms, infos, prof, clocks
 
     # headline: mixed path, inputs resident in HBM
-    ms_mixed, infos, prof, clocks = timed(lib.PRECISION_MIXED, args.steps, args.warmup, profile=True)
+    ms_mixed, infos, prof, clocks = timed(lib.PRECISION_MIXED, P["precond"], args.steps, args.warmup, profile=True)
     ms_mixed = max_over_ranks(pg, ms_mixed, local)
     out = {"metric": METRIC, "value": ms_mixed / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config_dict(A, "mixed")}
+           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": config_dict(A, B, "mixed")}
     info = infos[-1]
-    out["solve"] = {k: info[k] for k in ("cycles", "refine_cycles", "mv_A", "prec_apply", "nconv", "max_resid")}
+    out["solve"] = {k: info[k] for k in ("cycles", "refine_cycles", "mv_A", "mv_B", "prec_apply", "nconv",
+                                         "max_resid")}
     out["gpu_launches"] = int(sum(i["launches"] for i in infos))
     out["clocks"] = clocks
+    if setup:
+        out["setup"] = setup
     if world > 1:
         out["solves_per_s"] = world * 1e3 / ms_mixed
 
@@ -305,51 +400,69 @@ def run_ours(args, world, rank, local, pg):
         nl, tms, by = fam[dom]
         achieved = by / (tms / 1e3) / 1e9
         out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                           "frac": achieved / hbm_peak, "peak_source": peak_src, "traffic": traffic_for(dom),
+                           "frac": achieved / hbm_peak, "peak_source": peak_src,
+                           "traffic": traffic_for(dom) if P["key"] == "diffusion128" else None,
                            "launches": nl, "avg_launch_us": tms * 1e3 / nl,
                            "algorithmic_bytes_per_launch": by / nl}
     tot = sum(v[1] for v in prof.values()) or 1.0
     out["kernel_time_share"] = {k: round(v[1] / tot, 4) for k, v in sorted(prof.items(), key=lambda x: -x[1][1])}
+    out["kernel_gbs"] = {k: round(v[2] / (v[1] / 1e3) / 1e9, 1) for k, v in prof.items() if v[1] > 0 and v[2] > 0}
     for key in ("spmv_scaled", "spmv"):
         if key in prof and prof[key][1] > 0:
             nl, tms, by = prof[key]
             out["spmv_gbs"] = by / (tms / 1e3) / 1e9
             break
 
-    # comparison: plain FP64 path on the same matrix
+    # comparisons on the same operator: the plain FP64 path (and, for the
+    # learned preconditioner, Jacobi and classical FSAI in both precisions)
+    fp64_cycles = None
     if not args.no_fp64:
-        ms64, infos64, _, _ = timed(lib.PRECISION_FP64, max(1, args.steps), 1)
-        ms64 = max_over_ranks(pg, ms64, local)
-        out["fp64_seconds"] = ms64 / 1e3
-        out["fp64_cycles"] = infos64[-1]["cycles"]
-        out["speedup_vs_fp64"] = ms64 / ms_mixed
+        runs = [("fp64", lib.PRECISION_FP64, P["precond"])]
+        if P["precond"] == "fsai_learned":
+            runs += [("jacobi_mixed", lib.PRECISION_MIXED, "jacobi"), ("fsai_mixed", lib.PRECISION_MIXED, "fsai"),
+                     ("jacobi_fp64", lib.PRECISION_FP64, "jacobi"), ("fsai_fp64", lib.PRECISION_FP64, "fsai")]
+        comp = {}
+        for name, prec, pc in runs:
+            ms, inf, _, _ = timed(prec, pc, max(1, args.steps) if name == "fp64" else 1, 1)
+            ms = max_over_ranks(pg, ms, local)
+            comp[name] = {"seconds": ms / 1e3, "cycles": inf[-1]["cycles"], "mv_A": inf[-1]["mv_A"],
+                          "max_resid": inf[-1]["max_resid"]}
+        out["fp64_seconds"] = comp["fp64"]["seconds"]
+        out["fp64_cycles"] = fp64_cycles = comp["fp64"]["cycles"]
+        out["speedup_vs_fp64"] = comp["fp64"]["seconds"] * 1e3 / ms_mixed
+        if len(comp) > 1:
+            out["comparisons"] = comp
 
     # end to end: host CSR in pinned memory, host outputs
     if not args.no_e2e:
-        rp_h = torch.from_numpy(A.rowptr).pin_memory()
-        cl_h = torch.from_numpy(A.col).pin_memory()
-        vl_h = torch.from_numpy(A.val).pin_memory()
-        Ah = lib.make_csr(rp_h.numpy(), cl_h.numpy(), vl_h.numpy())
+        def to_host(M):
+            if M is None:
+                return None, 0
+            t = (torch.from_numpy(M.rowptr).pin_memory(), torch.from_numpy(M.col).pin_memory(),
+                 torch.from_numpy(M.val).pin_memory())
+            return lib.make_csr(t[0].numpy(), t[1].numpy(), t[2].numpy()), M.rowptr.nbytes + M.col.nbytes + M.val.nbytes
+
+        Ah, hA = to_host(A)
+        Bh, hB = to_host(B)
         ev_h = torch.zeros(p, dtype=torch.float64).pin_memory()
         X_h = torch.zeros((p, n), dtype=torch.float64).pin_memory()
         r_h = torch.zeros(p, dtype=torch.float64).pin_memory()
-        params = lib.make_params(P["p"], P["q"], P["k"], P["l"], P["tol"], 5000, P["seed"], lib.PRECOND_JACOBI,
-                                 lib.PRECISION_MIXED, 0)
+        prm = params(lib.PRECISION_MIXED, P["precond"], 0)
         ts = []
         for i in range(1 + args.steps):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            lib.trplk_solve(h, Ah, None, params, None, ev_h, X_h, r_h, lib.trplk_info())
+            lib.trplk_solve(h, Ah, Bh, prm, None, ev_h, X_h, r_h, lib.trplk_info())
             if i >= 1:
                 ts.append(time.perf_counter() - t0)
         e2e = max_over_ranks(pg, statistics.mean(ts), local)
-        h2d = A.rowptr.nbytes + A.col.nbytes + A.val.nbytes
+        h2d = hA + hB + (weights.nbytes if weights is not None else 0)
         d2h = ev_h.numel() * 8 + X_h.numel() * 8 + r_h.numel() * 8
         out["e2e"] = {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        secs, sample = oracle_sample(A)
+        secs, sample = oracle_sample(A, B, fp64_cycles)
         out["cpu_baseline"] = {"value": secs, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
                                "sample": sample}
     h.close()

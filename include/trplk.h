@@ -266,6 +266,13 @@ trplk_status trplk_project_noalloc(int dtype, int64_t n, int64_t ld, int w, cons
 /* Number of packed MLP parameters (TRPLK_MLP_PARAMS). */
 int trplk_mlp_param_count(void);
 
+/* Starting weights for training (host, no GPU): W1, W2 He-normal
+ * (variance 2/fan_in, SplitMix64 counter stream of `seed` through
+ * Box-Muller), W3 = 0, biases 0 except b3[c] = log(e - 1), so that
+ * softplus(o_c) = 1 and G = D^-1/2: training starts from Jacobi.
+ * weights: host float[TRPLK_MLP_PARAMS]; EINVAL if NULL. */
+trplk_status trplk_fsai_mlp_init(float* weights, uint64_t seed);
+
 /* G's values in the order of A's lower pattern.  kind 0: classical FSAI
  * (row i solves A[P_i, P_i] g = e_i, scaled so (G A G^T)_ii = 1; rows of at
  * most 16 lower entries); kind 1: learned (dims = nx, ny, nz of a 7-point

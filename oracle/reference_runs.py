@@ -30,6 +30,17 @@ def workloads():
                              p=10, q=40, k=15, l=1, tol=1e-8, seed=0),
         # 2D 5-point Laplacian on 100x100, 5 smallest, Jacobi, q=20, p_hat=8, +K=5, tol 1e-8
         "laplace100": dict(build=lambda: (W.laplacian_2d(100), None), p=5, q=20, k=8, l=5, tol=1e-8, seed=0),
+        # Q1 stiffness/mass pencil on 96^3 elements, E ~ U[1,10] (seed 2), 20 smallest, q=50, p_hat=25, +K=1
+        "q1pencil96": dict(build=lambda: W.fem_q1_pencil(96, np.random.default_rng(2).uniform(1.0, 10.0,
+                                                                                            (96, 96, 96))),
+                           p=20, q=50, k=25, l=1, tol=1e-8, seed=0),
+        # L + 1e-3 I of a Chung-Lu graph (2^22 vertices, mean degree 16, gamma 2.1, seed 3, largest component),
+        # 16 smallest, q=40, p_hat=20, +K=1
+        "chunglu22": dict(build=lambda: (W.chung_lu_laplacian(1 << 22, 16.0, 2.1, 3), None),
+                          p=16, q=40, k=20, l=1, tol=1e-8, seed=0),
+        # anisotropic 7-point diffusion on 128^3 (seed 2000), 20 smallest, q=50, p_hat=25, +K=1
+        "aniso128": dict(build=lambda: (W.anisotropic_diffusion(128, 2000), None),
+                         p=20, q=50, k=25, l=1, tol=1e-8, seed=0),
     }
 
 

@@ -83,6 +83,7 @@ def _load():
         "trplk_check_residuals": (st, [vp, C.POINTER(trplk_csr), C.POINTER(trplk_csr), i64, i32, vp, vp, dbl, vp]),
         "trplk_project_noalloc": (st, [i32, i64, i64, i32, vp, vp, vp, vp]),
         "trplk_mlp_param_count": (C.c_int, []),
+        "trplk_fsai_mlp_init": (st, [vp, C.c_uint64]),
         "trplk_fsai_values": (st, [vp, C.POINTER(trplk_csr), i32, vp, vp, i32, vp, C.POINTER(C.c_int64)]),
         "trplk_fsai_apply": (st, [vp, C.POINTER(trplk_csr), vp, vp, vp]),
         "trplk_fsai_loss_grad": (st, [vp, C.POINTER(trplk_csr), vp, vp, i32, vp, i32, dbl, vp, vp]),
@@ -263,6 +264,15 @@ def trplk_fsai_train(h, ops, dims, tp, weights, iters=None):
     losses = np.zeros(max(tp.iters, 1))
     h.check(LIB.trplk_fsai_train(h.h, arr, d, len(ops), C.byref(tp), ptr(weights), ptr(losses)))
     return losses[:tp.iters]
+
+
+def trplk_fsai_mlp_init(seed=0):
+    """Starting MLP weights (FP32 packed) from the library's initialiser."""
+    w = np.zeros(MLP_PARAMS, np.float32)
+    rc = LIB.trplk_fsai_mlp_init(ptr(w), int(seed))
+    if rc != OK:
+        raise TrplkError(rc, "trplk_fsai_mlp_init failed")
+    return w
 
 
 def pack_mlp(p):

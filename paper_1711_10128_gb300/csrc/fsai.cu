@@ -794,6 +794,30 @@ extern "C" {
 
 int trplk_mlp_param_count(void) { return kNParams; }
 
+trplk_status trplk_fsai_mlp_init(float* weights, uint64_t seed) {
+  if (!weights) return TRPLK_EINVAL;
+  // SplitMix64 (Steele, Lea, Flood 2014) on a counter, 53-bit uniforms in
+  // (0, 1], standard normals by the Box-Muller transform
+  uint64_t ctr = 0;
+  auto uniform = [&]() {
+    uint64_t z = (seed ^ ctr++) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((z >> 11) + 1) * (1.0 / 9007199254740992.0);
+  };
+  auto normal = [&]() {
+    const double u1 = uniform(), u2 = uniform();
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  };
+  float* P = weights;
+  for (int i = 0; i < kNParams; ++i) P[i] = 0.0f;
+  for (int i = 0; i < 64 * 8; ++i) P[i] = (float)(normal() * std::sqrt(2.0 / 8.0));               // W1
+  for (int i = 0; i < 64 * 64; ++i) P[576 + i] = (float)(normal() * std::sqrt(2.0 / 64.0));      // W2
+  P[kNParams - 7 + 3] = (float)std::log(std::expm1(1.0));                                          // b3[c]
+  return TRPLK_OK;
+}
+
 trplk_status trplk_fsai_values(trplk_handle* h, const trplk_csr* A, int kind, const int32_t* dims,
                                const float* weights, int bf16, double* g, int64_t* nnz_lower) {
   return guarded(h, [&]() -> trplk_status {

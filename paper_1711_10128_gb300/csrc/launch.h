@@ -92,7 +92,22 @@ struct DevCsr {
   const int64_t* sl_ptr = nullptr;   // [nslices + 1], multiples of 32
   const int32_t* sl_col = nullptr;
   const S* sl_val = nullptr;
+  // hybrid layout for rows of very unequal length (power-law graphs): the
+  // SELL slices cover only the rows listed in sl_perm (rows of at most
+  // kShortRow entries, sorted by descending length; null = all rows in
+  // order); long_rows lists the others, longest first: the first n_long_cta
+  // (more than kWarpRow entries) get a CTA each, the next n_long_warp a warp
+  // each, both reading the CSR arrays above
+  const int32_t* sl_perm = nullptr;
+  int64_t sl_rows = 0;               // rows in the SELL part (n without sl_perm)
+  const int32_t* long_rows = nullptr;
+  int64_t n_long_cta = 0, n_long_warp = 0;
 };
+
+constexpr int kShortRow = 32;    // longest row kept in the SELL part of a hybrid
+constexpr int kWarpRow = 1024;   // longest row given one warp; longer: one CTA
+constexpr int kHybBuckets = 61;  // length classes of the hybrid's row sort
+constexpr int kHybChunk = 1024;  // rows per warp in the sort kernels
 
 // ---- SpMV (spmv.cu)
 // y = A x.
@@ -104,12 +119,21 @@ template <typename S>
 void spmv_scaled(const Ctx& c, const DevCsr<S>& A, const S* x, const double* scale, S* y, S* g,
                  const S* bx, S* bg);
 
-// SELL-32 construction: lens[s] = longest row of slice s; then, given the
-// slice offsets, scatter column indices (when col != nullptr) and values.
-void sell_lengths(const Ctx& c, int64_t n, const int64_t* rowptr, int32_t* lens);
+// SELL-32 construction over the m rows perm[0..m) (perm null: rows 0..m-1):
+// lens[s] = longest row of slice s; then, given the slice offsets, scatter
+// column indices (when sl_col != nullptr) and values.
+void sell_lengths(const Ctx& c, int64_t m, const int64_t* rowptr, const int32_t* perm, int32_t* lens);
+// Hybrid row order: per chunk of kHybChunk rows, counts of every length class
+// (hist[chunk * kHybBuckets + b]); then, from per-chunk starting offsets, the
+// stable counting-sort scatter order[pos] = row.
+void hyb_hist(const Ctx& c, int64_t n, const int64_t* rowptr, int32_t* hist);
+void hyb_scatter(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* offs, int32_t* order);
+// length class of a row: [0, 22) one CTA, [22, 28) one warp, [28, 61) SELL
+inline int hyb_class_end_cta() { return 22; }
+inline int hyb_class_end_warp() { return 28; }
 template <typename S>
-void sell_fill(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
-               const int64_t* sl_ptr, int32_t* sl_col, S* sl_val);
+void sell_fill(const Ctx& c, int64_t m, const int64_t* rowptr, const int32_t* col, const double* val,
+               const int32_t* perm, const int64_t* sl_ptr, int32_t* sl_col, S* sl_val);
 
 // ---- tall-skinny passes (ts.cu).  All vectors have ld rows (zero padded).
 template <typename S>

@@ -24,34 +24,104 @@ using namespace trplk;
 
 // Build the SELL-32 copy of a device CSR (values from the FP64 array; an
 // FP32 copy too when f32 != nullptr) unless padding would add more than 25%.
-void attach_sell(trplk_handle* h, DevCsr<double>& d, const std::string& tag, DevCsr<float>* f32) {
+namespace {
+// SELL-32 over the m rows perm[0..m) (perm null: rows 0..m-1): slice offsets
+// from the slice lengths, then column indices and FP64 (and FP32) values.
+void build_sell(trplk_handle* h, DevCsr<double>& d, const std::string& tag, DevCsr<float>* f32, int64_t m,
+                const int32_t* perm, const std::vector<int64_t>& ptr) {
   const Ctx& c = h->ctx;
-  const int64_t nslices = (d.n + 31) / 32;
-  auto* lens = static_cast<int32_t*>(h->get(tag + ".sl_len", nslices * sizeof(int32_t)));
-  sell_lengths(c, d.n, d.rowptr, lens);
-  std::vector<int32_t> hl(nslices);
-  TRPLK_CUDA_TRY(cudaMemcpyAsync(hl.data(), lens, nslices * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
-  h->sync();
-  std::vector<int64_t> ptr(nslices + 1, 0);
-  for (int64_t s = 0; s < nslices; ++s) ptr[s + 1] = ptr[s] + 32 * (int64_t)hl[s];
+  const int64_t nslices = (m + 31) / 32;
   const int64_t padded = ptr[nslices];
-  if ((double)padded > 1.25 * (double)d.nnz + 32.0 * nslices) return;
   auto* sp = static_cast<int64_t*>(h->get(tag + ".sl_ptr", (nslices + 1) * sizeof(int64_t)));
-  auto* sc = static_cast<int32_t*>(h->get(tag + ".sl_col", padded * sizeof(int32_t)));
-  auto* sv = static_cast<double*>(h->get(tag + ".sl_val", padded * sizeof(double)));
+  auto* sc = static_cast<int32_t*>(h->get(tag + ".sl_col", std::max<int64_t>(padded, 1) * sizeof(int32_t)));
+  auto* sv = static_cast<double*>(h->get(tag + ".sl_val", std::max<int64_t>(padded, 1) * sizeof(double)));
   TRPLK_CUDA_TRY(cudaMemcpyAsync(sp, ptr.data(), (nslices + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
-  sell_fill<double>(c, d.n, d.rowptr, d.col, d.val, sp, sc, sv);
+  sell_fill<double>(c, m, d.rowptr, d.col, d.val, perm, sp, sc, sv);
   d.sl_ptr = sp;
   d.sl_col = sc;
   d.sl_val = sv;
   if (f32) {
-    auto* svf = static_cast<float*>(h->get(tag + ".sl_valf", padded * sizeof(float)));
-    sell_fill<float>(c, d.n, d.rowptr, d.col, d.val, sp, nullptr, svf);
+    auto* svf = static_cast<float*>(h->get(tag + ".sl_valf", std::max<int64_t>(padded, 1) * sizeof(float)));
+    sell_fill<float>(c, m, d.rowptr, d.col, d.val, perm, sp, nullptr, svf);
     f32->sl_ptr = sp;
     f32->sl_col = sc;
     f32->sl_val = svf;
   }
   h->sync();   // ptr (host vector) must stay alive until its copy finished
+}
+
+std::vector<int64_t> slice_offsets(trplk_handle* h, const std::string& tag, int64_t m, const int64_t* rowptr,
+                                   const int32_t* perm) {
+  const Ctx& c = h->ctx;
+  const int64_t nslices = (m + 31) / 32;
+  std::vector<int64_t> ptr(nslices + 1, 0);
+  if (nslices == 0) return ptr;
+  auto* lens = static_cast<int32_t*>(h->get(tag + ".sl_len", nslices * sizeof(int32_t)));
+  sell_lengths(c, m, rowptr, perm, lens);
+  std::vector<int32_t> hl(nslices);
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(hl.data(), lens, nslices * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  h->sync();
+  for (int64_t s = 0; s < nslices; ++s) ptr[s + 1] = ptr[s] + 32 * (int64_t)hl[s];
+  return ptr;
+}
+}  // namespace
+
+// SELL-32 copy of a device CSR.  When plain slices would pad the entries by
+// more than 25% (rows of very unequal length), the hybrid form is built
+// instead: rows ordered by length class (a stable counting sort: per-chunk
+// class counts on the device, their prefix sums here), the longest rows
+// handled by a CTA or a warp each from the CSR arrays, the rest in slices.
+void attach_sell(trplk_handle* h, DevCsr<double>& d, const std::string& tag, DevCsr<float>* f32) {
+  const Ctx& c = h->ctx;
+  const int64_t n = d.n;
+  std::vector<int64_t> ptr = slice_offsets(h, tag, n, d.rowptr, nullptr);
+  const int64_t nslices = (n + 31) / 32;
+  if ((double)ptr[nslices] <= 1.25 * (double)d.nnz + 32.0 * nslices) {
+    build_sell(h, d, tag, f32, n, nullptr, ptr);
+    return;
+  }
+  const int64_t chunks = (n + kHybChunk - 1) / kHybChunk;
+  auto* hist = static_cast<int32_t*>(h->get(tag + ".hyb_hist", chunks * kHybBuckets * sizeof(int32_t)));
+  auto* order = static_cast<int32_t*>(h->get(tag + ".hyb_order", n * sizeof(int32_t)));
+  hyb_hist(c, n, d.rowptr, hist);
+  std::vector<int32_t> hh(chunks * kHybBuckets);
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(hh.data(), hist, hh.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  h->sync();
+  // offsets[chunk][b] = rows of classes < b + rows of class b in earlier chunks
+  std::vector<int64_t> total(kHybBuckets, 0);
+  for (int64_t ch = 0; ch < chunks; ++ch)
+    for (int b = 0; b < kHybBuckets; ++b) total[b] += hh[ch * kHybBuckets + b];
+  std::vector<int64_t> start(kHybBuckets + 1, 0);
+  for (int b = 0; b < kHybBuckets; ++b) start[b + 1] = start[b] + total[b];
+  std::vector<int32_t> offs(hh.size());
+  for (int b = 0; b < kHybBuckets; ++b) {
+    int64_t run = start[b];
+    for (int64_t ch = 0; ch < chunks; ++ch) {
+      offs[ch * kHybBuckets + b] = (int32_t)run;
+      run += hh[ch * kHybBuckets + b];
+    }
+  }
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(hist, offs.data(), offs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream));
+  hyb_scatter(c, n, d.rowptr, hist, order);
+  h->sync();   // offs (host vector) must stay alive until its copy finished
+  const int64_t n_cta = start[hyb_class_end_cta()];
+  const int64_t n_long = start[hyb_class_end_warp()];
+  const int64_t m = n - n_long;
+  const int32_t* perm = order + n_long;
+  std::vector<int64_t> hptr = slice_offsets(h, tag, m, d.rowptr, perm);
+  build_sell(h, d, tag, f32, m, perm, hptr);
+  d.sl_perm = perm;
+  d.sl_rows = m;
+  d.long_rows = order;
+  d.n_long_cta = n_cta;
+  d.n_long_warp = n_long - n_cta;
+  if (f32) {
+    f32->sl_perm = perm;
+    f32->sl_rows = m;
+    f32->long_rows = order;
+    f32->n_long_cta = n_cta;
+    f32->n_long_warp = n_long - n_cta;
+  }
 }
 
 

@@ -2,7 +2,10 @@
 //
 // SpMV (eq. (UpdateT), z = A g).  Operators whose rows have similar lengths
 // (stencils, FEM) are converted to SELL-32 at set-up and multiplied by
-// sell_spmv_kernel below; others use CSR-stream, one thread per row.  A CTA owns
+// sell_spmv_kernel below.  Operators with very unequal rows (power-law graphs)
+// get the hybrid form of the same kernel: rows sorted by length class, short
+// rows in SELL-32 slices, long rows one warp each, the longest one CTA each.
+// CSR-stream, one thread per row, serves matrices with neither copy.  A CTA owns
 // 256 consecutive rows; it streams the values and column indices of those
 // rows into shared memory with coalesced loads (the rows are contiguous in
 // CSR, so the whole block is one contiguous range), then each thread forms its
@@ -91,25 +94,98 @@ __global__ void __launch_bounds__(kRows) spmv_kernel(int64_t n, const int64_t* _
   }
 }
 
+template <typename S, bool SCALED>
+__device__ __forceinline__ void spmv_finish(int64_t row, S sum, const S* __restrict__ x, S* __restrict__ y,
+                                            const double* __restrict__ scale, S* __restrict__ g,
+                                            const S* __restrict__ bx, S* __restrict__ bg) {
+  if (SCALED) {
+    const S s = (S)(*scale);
+    y[row] = s * sum;
+    g[row] = s * x[row];
+    if (bx) bg[row] = s * bx[row];
+  } else {
+    y[row] = sum;
+  }
+}
+
+// One long CSR row: entries e0 + t, e0 + t + step, ... with four independent
+// chains (fixed order, so the result is deterministic).
+template <typename S>
+__device__ __forceinline__ S row_segment(int64_t e, int64_t re, int step, const int32_t* __restrict__ col,
+                                         const S* __restrict__ val, const S* __restrict__ x) {
+  S s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  for (; e + 3 * (int64_t)step < re; e += 4 * (int64_t)step) {
+    const int32_t c0 = __ldg(col + e), c1 = __ldg(col + e + step);
+    const int32_t c2 = __ldg(col + e + 2 * step), c3 = __ldg(col + e + 3 * step);
+    const S v0 = __ldg(val + e), v1 = __ldg(val + e + step), v2 = __ldg(val + e + 2 * step);
+    const S v3 = __ldg(val + e + 3 * step);
+    s0 = fmaS(v0, __ldg(x + c0), s0);
+    s1 = fmaS(v1, __ldg(x + c1), s1);
+    s2 = fmaS(v2, __ldg(x + c2), s2);
+    s3 = fmaS(v3, __ldg(x + c3), s3);
+  }
+  for (; e < re; e += step) s0 = fmaS(__ldg(val + e), __ldg(x + __ldg(col + e)), s0);
+  return (s0 + s1) + (s2 + s3);
+}
+
+template <typename S>
+__device__ __forceinline__ S warp_sum(S v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // SELL-32 matvec: one warp per 32-row slice, one lane per row.  The slice's
 // entries are stored column-major, so every load of values and column indices
 // is one coalesced 128/256-byte transaction and independent of the others;
 // no row-pointer chase and no shared-memory staging.
-template <typename S, bool SCALED>
-__global__ void __launch_bounds__(256) sell_spmv_kernel(int64_t n, int64_t nslices,
-                                                        const int64_t* __restrict__ sl_ptr,
-                                                        const int32_t* __restrict__ col,
-                                                        const S* __restrict__ val, const S* __restrict__ x,
-                                                        S* __restrict__ y, const double* __restrict__ scale,
-                                                        S* __restrict__ g, const S* __restrict__ bx,
-                                                        S* __restrict__ bg) {
-  const int64_t slice = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+// HYB: the grid starts with n_cta blocks that each own one of the longest
+// rows (256 threads stride the row, block reduction in a fixed order), then
+// blocks of 8 warps that each own one long row (lanes stride the row, xor
+// butterfly), then the SELL slices of the remaining rows, whose positions map
+// to rows through perm.  Heavy rows come first so they start first.
+template <typename S, bool SCALED, bool HYB>
+__global__ void __launch_bounds__(256) sell_spmv_kernel(
+    int64_t m, int64_t nslices, const int64_t* __restrict__ sl_ptr, const int32_t* __restrict__ sl_col,
+    const S* __restrict__ sl_val, const int32_t* __restrict__ perm, const int32_t* __restrict__ long_rows,
+    int64_t n_cta, int64_t n_warp, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+    const S* __restrict__ val, const S* __restrict__ x, S* __restrict__ y, const double* __restrict__ scale,
+    S* __restrict__ g, const S* __restrict__ bx, S* __restrict__ bg) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t b = blockIdx.x;
+  if (HYB) {
+    if (b < n_cta) {   // one CTA per row
+      __shared__ S red[8];
+      const int64_t row = long_rows[b];
+      const S v = warp_sum(row_segment<S>(rowptr[row] + threadIdx.x, rowptr[row + 1], 256, col, val, x));
+      if (lane == 0) red[warp] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        S t = red[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) t += red[w];
+        spmv_finish<S, SCALED>(row, t, x, y, scale, g, bx, bg);
+      }
+      return;
+    }
+    b -= n_cta;
+    const int64_t wblocks = (n_warp + 7) / 8;
+    if (b < wblocks) {   // one warp per row
+      const int64_t w = b * 8 + warp;
+      if (w >= n_warp) return;
+      const int64_t row = long_rows[n_cta + w];
+      const S v = warp_sum(row_segment<S>(rowptr[row] + lane, rowptr[row + 1], 32, col, val, x));
+      if (lane == 0) spmv_finish<S, SCALED>(row, v, x, y, scale, g, bx, bg);
+      return;
+    }
+    b -= wblocks;
+  }
+  const int64_t slice = b * 8 + warp;
   if (slice >= nslices) return;
   const int64_t base = sl_ptr[slice];
   const int len = (int)((sl_ptr[slice + 1] - base) >> 5);
-  const S* vp = val + base + lane;
-  const int32_t* cp = col + base + lane;
+  const S* vp = sl_val + base + lane;
+  const int32_t* cp = sl_col + base + lane;
   S sum = 0;
   int j = 0;
   for (; j + 4 <= len; j += 4) {
@@ -136,17 +212,8 @@ __global__ void __launch_bounds__(256) sell_spmv_kernel(int64_t n, int64_t nslic
     if (r > 1) sum = fmaS(v1, x1, sum);
     if (r > 2) sum = fmaS(v2, x2, sum);
   }
-  const int64_t row = slice * 32 + lane;
-  if (row < n) {
-    if (SCALED) {
-      const S s = (S)(*scale);
-      y[row] = s * sum;
-      g[row] = s * x[row];
-      if (bx) bg[row] = s * bx[row];
-    } else {
-      y[row] = sum;
-    }
-  }
+  const int64_t pos = slice * 32 + lane;
+  if (pos < m) spmv_finish<S, SCALED>(HYB ? (int64_t)perm[pos] : pos, sum, x, y, scale, g, bx, bg);
 }
 
 template <typename S>
@@ -154,17 +221,29 @@ void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const doubl
                  const S* bx, S* bg, bool scaled) {
   if (A.n == 0) return;
   if (A.sl_ptr) {
-    const int64_t nslices = (A.n + 31) / 32;
-    const int64_t blocks = (nslices * 32 + 255) / 256;
+    const bool hyb = A.sl_perm || A.long_rows;
+    const int64_t m = hyb ? A.sl_rows : A.n;
+    const int64_t nslices = (m + 31) / 32;
+    const int64_t nlong = A.n_long_cta + A.n_long_warp;
+    const int64_t blocks = (hyb ? A.n_long_cta + (A.n_long_warp + 7) / 8 : 0) + (nslices + 7) / 8;
+    if (blocks > 0x7fffffff) throw Error(TRPLK_EINVAL, "matrix too large");
+    // algorithmic bytes: values + column indices once, slice offsets, row
+    // map and long-row pointers, x once, y (and the scaled copies) once
     double bytes = (double)A.nnz * (sizeof(S) + 4) + (double)(nslices + 1) * 8 + 2.0 * A.n * sizeof(S);
+    if (hyb) bytes += (double)m * 4 + (double)nlong * 20;
     if (scaled) bytes += (double)A.n * sizeof(S) * (bx ? 3 : 1);
     ProfScope ps(c, scaled ? PK_SPMV_SCALED : PK_SPMV, bytes);
-    if (scaled)
-      sell_spmv_kernel<S, true><<<(unsigned)blocks, 256, 0, c.stream>>>(A.n, nslices, A.sl_ptr, A.sl_col, A.sl_val,
-                                                                         x, y, scale, g, bx, bg);
-    else
-      sell_spmv_kernel<S, false><<<(unsigned)blocks, 256, 0, c.stream>>>(A.n, nslices, A.sl_ptr, A.sl_col, A.sl_val,
-                                                                          x, y, nullptr, nullptr, nullptr, nullptr);
+    const unsigned gb = (unsigned)(blocks > 0 ? blocks : 1);
+#define TRPLK_SELL(SC, HY)                                                                                  \
+  sell_spmv_kernel<S, SC, HY><<<gb, 256, 0, c.stream>>>(m, nslices, A.sl_ptr, A.sl_col, A.sl_val, A.sl_perm,  \
+                                                        A.long_rows, A.n_long_cta, A.n_long_warp, A.rowptr,  \
+                                                        A.col, A.val, x, y, scale, g, bx, bg)
+    if (scaled) {
+      if (hyb) TRPLK_SELL(true, true); else TRPLK_SELL(true, false);
+    } else {
+      if (hyb) TRPLK_SELL(false, true); else TRPLK_SELL(false, false);
+    }
+#undef TRPLK_SELL
     check_launch("sell_spmv_kernel");
     return;
   }
@@ -250,28 +329,35 @@ __global__ void jacobi_dinv_kernel(int64_t n, const int64_t* __restrict__ rowptr
   }
 }
 
-__global__ void sell_lengths_kernel(int64_t n, const int64_t* __restrict__ rowptr, int32_t* __restrict__ lens) {
+__global__ void sell_lengths_kernel(int64_t m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ perm,
+                                    int32_t* __restrict__ lens) {
   const int64_t slice = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  const int64_t row = slice * 32 + lane;
-  int len = row < n ? (int)(rowptr[row + 1] - rowptr[row]) : 0;
+  const int64_t pos = slice * 32 + lane;
+  int len = 0;
+  if (pos < m) {
+    const int64_t row = perm ? (int64_t)perm[pos] : pos;
+    len = (int)(rowptr[row + 1] - rowptr[row]);
+  }
   for (int off = 16; off > 0; off >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, off));
-  if (lane == 0 && slice * 32 < n) lens[slice] = len;
+  if (lane == 0 && slice * 32 < m) lens[slice] = len;
 }
 
 template <typename S>
-__global__ void sell_fill_kernel(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                 const double* __restrict__ val, const int64_t* __restrict__ sl_ptr,
-                                 int32_t* __restrict__ sl_col, S* __restrict__ sl_val) {
+__global__ void sell_fill_kernel(int64_t m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                 const double* __restrict__ val, const int32_t* __restrict__ perm,
+                                 const int64_t* __restrict__ sl_ptr, int32_t* __restrict__ sl_col,
+                                 S* __restrict__ sl_val) {
   const int64_t slice = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (slice * 32 >= n) return;
-  const int64_t row = slice * 32 + lane;
+  if (slice * 32 >= m) return;
+  const int64_t pos = slice * 32 + lane;
+  const int64_t row = pos < m ? (perm ? (int64_t)perm[pos] : pos) : -1;
   const int64_t base = sl_ptr[slice];
   const int len = (int)((sl_ptr[slice + 1] - base) >> 5);
-  const int64_t rs = row < n ? rowptr[row] : 0;
-  const int rl = row < n ? (int)(rowptr[row + 1] - rs) : 0;
-  const int32_t pad_col = (int32_t)(row < n ? row : 0);
+  const int64_t rs = row >= 0 ? rowptr[row] : 0;
+  const int rl = row >= 0 ? (int)(rowptr[row + 1] - rs) : 0;
+  const int32_t pad_col = (int32_t)(row >= 0 ? row : 0);
   for (int j = 0; j < len; ++j) {
     const int64_t o = base + 32 * (int64_t)j + lane;
     if (j < rl) {
@@ -281,6 +367,58 @@ __global__ void sell_fill_kernel(int64_t n, const int64_t* __restrict__ rowptr, 
       if (sl_col) sl_col[o] = pad_col;
       sl_val[o] = (S)0;
     }
+  }
+}
+
+// length class of a row: the longest first.  [0, 22): more than kWarpRow
+// entries, by descending floor(log2 len); [22, 28): kShortRow+1 .. kWarpRow,
+// likewise; [28, 61): 0 .. kShortRow entries, by descending length.
+__device__ __forceinline__ int hyb_bucket(int64_t len) {
+  const int lg = 63 - __clzll((unsigned long long)(len > 0 ? len : 1));
+  if (len > kWarpRow) return lg >= 31 ? 0 : 31 - lg;
+  if (len > kShortRow) return 22 + (10 - lg);
+  return 28 + (kShortRow - (int)len);
+}
+
+// one warp per chunk of kHybChunk rows: class counts of the chunk
+__global__ void __launch_bounds__(256) hyb_hist_kernel(int64_t n, const int64_t* __restrict__ rowptr,
+                                                       int32_t* __restrict__ hist) {
+  __shared__ int cnt[8][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t chunk = (int64_t)blockIdx.x * 8 + warp;
+  for (int b = lane; b < 64; b += 32) cnt[warp][b] = 0;
+  __syncwarp();
+  const int64_t r0 = chunk * kHybChunk;
+  for (int i = lane; i < kHybChunk; i += 32) {
+    const int64_t row = r0 + i;
+    if (row < n) atomicAdd(&cnt[warp][hyb_bucket(rowptr[row + 1] - rowptr[row])], 1);
+  }
+  __syncwarp();
+  if (r0 < n)
+    for (int b = lane; b < kHybBuckets; b += 32) hist[chunk * kHybBuckets + b] = cnt[warp][b];
+}
+
+// stable scatter: rows of a chunk are visited in order 32 at a time; lanes of
+// one class find their rank among themselves with a match + popcount
+__global__ void __launch_bounds__(256) hyb_scatter_kernel(int64_t n, const int64_t* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ offs,
+                                                          int32_t* __restrict__ order) {
+  __shared__ int off[8][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t chunk = (int64_t)blockIdx.x * 8 + warp;
+  const int64_t r0 = chunk * kHybChunk;
+  if (r0 >= n) return;   // warp-uniform
+  for (int b = lane; b < kHybBuckets; b += 32) off[warp][b] = offs[chunk * kHybBuckets + b];
+  __syncwarp();
+  for (int i = 0; i < kHybChunk; i += 32) {
+    const int64_t row = r0 + i + lane;
+    const int b = row < n ? hyb_bucket(rowptr[row + 1] - rowptr[row]) : 63;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (row < n) order[off[warp][b] + rank] = (int32_t)row;
+    __syncwarp();
+    if (row < n && rank == 0) off[warp][b] += __popc(peers);
+    __syncwarp();
   }
 }
 
@@ -339,27 +477,43 @@ void axpby_shift(const Ctx& c, int64_t ld, const S* x, const S* y, double rho, S
   check_launch("axpby_shift");
 }
 
-void sell_lengths(const Ctx& c, int64_t n, const int64_t* rowptr, int32_t* lens) {
-  const int64_t nslices = (n + 31) / 32;
+void sell_lengths(const Ctx& c, int64_t m, const int64_t* rowptr, const int32_t* perm, int32_t* lens) {
+  const int64_t nslices = (m + 31) / 32;
+  if (nslices == 0) return;
   ProfScope ps(c, PK_OTHER, 0.0);
-  sell_lengths_kernel<<<(unsigned)((nslices * 32 + 255) / 256), 256, 0, c.stream>>>(n, rowptr, lens);
+  sell_lengths_kernel<<<(unsigned)((nslices * 32 + 255) / 256), 256, 0, c.stream>>>(m, rowptr, perm, lens);
   check_launch("sell_lengths");
 }
 
 template <typename S>
-void sell_fill(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
-               const int64_t* sl_ptr, int32_t* sl_col, S* sl_val) {
-  const int64_t nslices = (n + 31) / 32;
+void sell_fill(const Ctx& c, int64_t m, const int64_t* rowptr, const int32_t* col, const double* val,
+               const int32_t* perm, const int64_t* sl_ptr, int32_t* sl_col, S* sl_val) {
+  const int64_t nslices = (m + 31) / 32;
+  if (nslices == 0) return;
   ProfScope ps(c, PK_OTHER, 0.0);
-  sell_fill_kernel<S><<<(unsigned)((nslices * 32 + 255) / 256), 256, 0, c.stream>>>(n, rowptr, col, val, sl_ptr,
-                                                                                    sl_col, sl_val);
+  sell_fill_kernel<S><<<(unsigned)((nslices * 32 + 255) / 256), 256, 0, c.stream>>>(m, rowptr, col, val, perm,
+                                                                                    sl_ptr, sl_col, sl_val);
   check_launch("sell_fill");
 }
 
-template void sell_fill<double>(const Ctx&, int64_t, const int64_t*, const int32_t*, const double*, const int64_t*,
-                                int32_t*, double*);
-template void sell_fill<float>(const Ctx&, int64_t, const int64_t*, const int32_t*, const double*, const int64_t*,
-                               int32_t*, float*);
+void hyb_hist(const Ctx& c, int64_t n, const int64_t* rowptr, int32_t* hist) {
+  const int64_t chunks = (n + kHybChunk - 1) / kHybChunk;
+  ProfScope ps(c, PK_OTHER, 0.0);
+  hyb_hist_kernel<<<(unsigned)((chunks + 7) / 8), 256, 0, c.stream>>>(n, rowptr, hist);
+  check_launch("hyb_hist");
+}
+
+void hyb_scatter(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* offs, int32_t* order) {
+  const int64_t chunks = (n + kHybChunk - 1) / kHybChunk;
+  ProfScope ps(c, PK_OTHER, 0.0);
+  hyb_scatter_kernel<<<(unsigned)((chunks + 7) / 8), 256, 0, c.stream>>>(n, rowptr, offs, order);
+  check_launch("hyb_scatter");
+}
+
+template void sell_fill<double>(const Ctx&, int64_t, const int64_t*, const int32_t*, const double*, const int32_t*,
+                                const int64_t*, int32_t*, double*);
+template void sell_fill<float>(const Ctx&, int64_t, const int64_t*, const int32_t*, const double*, const int32_t*,
+                               const int64_t*, int32_t*, float*);
 template void spmv<double>(const Ctx&, const DevCsr<double>&, const double*, double*);
 template void spmv<float>(const Ctx&, const DevCsr<float>&, const float*, float*);
 template void spmv_scaled<double>(const Ctx&, const DevCsr<double>&, const double*, const double*, double*,

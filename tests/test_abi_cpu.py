@@ -57,3 +57,19 @@ def test_create_without_gpu_fails_cleanly(binding):
     with pytest.raises(binding.TrplkError) as e:
         binding.Handle(0)
     assert e.value.code == binding.EINVAL
+
+
+def test_mlp_init_starts_from_jacobi(binding):
+    """Host-only initialiser: W3 = 0 and softplus(b3[c]) = 1, so the learned
+    G starts at D^-1/2; He-normal hidden weights; same seed, same weights."""
+    import numpy as np
+    w = binding.trplk_fsai_mlp_init(7)
+    p = binding.unpack_mlp(w)
+    assert np.all(p["W3"] == 0) and np.all(p["b1"] == 0) and np.all(p["b2"] == 0)
+    assert abs(np.logaddexp(0.0, p["b3"][3]) - 1.0) < 1e-6
+    assert np.count_nonzero(p["b3"]) == 1
+    assert abs(p["W1"].std() - np.sqrt(2 / 8)) < 0.1 * np.sqrt(2 / 8)
+    assert abs(p["W2"].std() - np.sqrt(2 / 64)) < 0.05 * np.sqrt(2 / 64)
+    assert abs(p["W2"].mean()) < 0.01
+    assert np.array_equal(w, binding.trplk_fsai_mlp_init(7))
+    assert not np.array_equal(w, binding.trplk_fsai_mlp_init(8))

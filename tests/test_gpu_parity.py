@@ -102,6 +102,43 @@ def test_spmv_matches_oracle(lib, h, name, prec):
         assert np.all(np.abs(y.cpu().numpy().astype(np.float64) - ref) <= 1e-6 * scale)
 
 
+def hub_matrix(n=6000, seed=7):
+    """Rows of every length class of the hybrid SpMV: two hubs of more than
+    1024 entries, rows of 33..1024, short rows of 1..32, and empty rows."""
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(0, 33, n)
+    lens[rng.choice(n, 300, replace=False)] = 0
+    lens[rng.choice(n, 200, replace=False)] = rng.integers(33, 1025, 200)
+    lens[[5, 4000]] = [3000, 1500]
+    rows = []
+    for i, m in enumerate(lens):
+        rows.append(np.sort(rng.choice(n, int(m), replace=False)))
+    col = np.concatenate(rows).astype(np.int32)
+    rowptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    val = rng.standard_normal(col.size)
+    return W.Csr(rowptr, col, val)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_spmv_hybrid_rows_match_oracle(lib, h, prec):
+    """The hybrid form (rows sorted by length class: CTA per row, warp per row,
+    SELL slices) against the oracle's matvec, empty rows included."""
+    A = hub_matrix()
+    x = np.random.default_rng(2).standard_normal(A.n)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    vals = A.val if prec == "f64" else A.val.astype(np.float32).astype(np.float64)
+    xs = x if prec == "f64" else x.astype(np.float32).astype(np.float64)
+    As = sp.csr_matrix((vals, A.col, A.rowptr), shape=(A.n, A.n))
+    y = torch.full((A.n,), 7.0, dtype=dt, device="cuda")
+    lib.trplk_spmv(h, dev_csr(lib, A, dt), dev(xs.astype(np.float64 if prec == "f64" else np.float32)), y)
+    ref = O.spmv(As, xs)
+    scale = abs(As) @ np.abs(xs)
+    rel = 1e-14 if prec == "f64" else 1e-6
+    assert np.all(np.abs(y.cpu().numpy().astype(np.float64) - ref) <= rel * scale)
+    empty = np.flatnonzero(np.diff(A.rowptr) == 0)
+    assert empty.size > 0 and np.all(y.cpu().numpy()[empty] == 0)
+
+
 def test_spmv_full_size_sampled_rows(lib, h):
     """128^3 lognormal diffusion (n = 2,097,152): sampled rows against the
     oracle's row dot products."""
@@ -388,6 +425,54 @@ def test_mixed_precision_matches_oracle(lib, h):
     assert np.all(res <= 1e-10)
     assert np.all(np.abs(ev - ref["evals"]) <= 1e-10 * np.abs(ref["evals"]))
     assert np.allclose(X.T @ X, np.eye(p), atol=1e-11)
+
+
+def test_mixed_precision_generalized_pencil_matches_oracle(lib, h):
+    """The mixed path on the Q1 stiffness/mass pencil (B != I): FP32 basis with
+    B-images, FP64 refinement; eigenvalues against the FP64 oracle."""
+    N = 8
+    A, B = W.fem_q1_pencil(N, np.random.default_rng(2).uniform(1, 10, (N, N, N)))
+    As, Bs = A.to_scipy(), B.to_scipy()
+    p, q, k, l = 5, 20, 8, 1
+    X0 = W.start_block(A.n, k, 2)
+    ref = O.solve(As, Bs, p, q, k, l, 1e-9, X0, "jacobi")
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), dev_csr(lib, B), p=p, q=q, k=k, l=l, tol=1e-9, X0=X0,
+                                     precision=lib.PRECISION_MIXED)
+    assert rc == lib.OK and ref["status"] == O.OK
+    assert np.all(np.abs(ev - ref["evals"]) <= 1e-10 * np.abs(ref["evals"]))
+    assert np.allclose(X.T @ (Bs @ X), np.eye(p), atol=1e-11)
+    r = np.linalg.norm(As @ X - (Bs @ X) * ev, axis=0) / (O.norm1(As) * np.linalg.norm(X, axis=0))
+    assert np.all(r <= 1e-9)
+    # every orthogonalised vector costs one B matvec; a dropped +K column or an
+    # early end of the inner loop costs no A matvec, so only >= holds here
+    assert info["mv_B"] >= info["mv_A"]
+
+
+_CL_REF = {}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,mean,p", [(3000, 8.0, 6), (80000, 20.0, 4)])
+def test_chung_lu_laplacian_matches_oracle(lib, h, precision, n, mean, p):
+    """Shifted Laplacian of a Chung-Lu power-law graph (largest component;
+    the larger case has rows of more than 1024 entries, so every class of the
+    hybrid SpMV runs inside the solve): the smallest eigenvalue is the shift
+    exactly (constant vector), the rest match the oracle's."""
+    L = W.chung_lu_laplacian(n, mean, 2.1, 3)
+    Ls = L.to_scipy()
+    q, k, l = 24, 10, 1
+    X0 = W.start_block(L.n, k, 1)
+    if (n, p) not in _CL_REF:
+        _CL_REF[(n, p)] = O.solve(Ls, None, p, q, k, l, 1e-10, X0, "jacobi")
+    ref = _CL_REF[(n, p)]
+    prec = lib.PRECISION_FP64 if precision == "fp64" else lib.PRECISION_MIXED
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, L), None, p=p, q=q, k=k, l=l, tol=1e-10, X0=X0,
+                                     precision=prec)
+    assert rc == lib.OK and ref["status"] == O.OK
+    assert abs(ev[0] - 1e-3) <= 1e-12
+    assert np.all(np.abs(ev - ref["evals"]) <= 1e-10 * np.abs(ref["evals"]))
+    r = np.linalg.norm(Ls @ X - X * ev, axis=0) / (O.norm1(Ls) * np.linalg.norm(X, axis=0))
+    assert np.all(r <= 1e-10)
 
 
 def test_ragged_and_degenerate_edges(lib, h):
