@@ -328,9 +328,10 @@ trplk_status trplk_fsai_train(trplk_handle* h, const trplk_csr* ops, const int32
 trplk_status trplk_profile(trplk_handle* h, int enable);
 
 /* Totals since the last trplk_profile(h, 1) for one kernel family `kind`
- * (0 <= kind < 12; see trplk_profile_kind_name): number of launches, summed
- * event time in milliseconds and summed algorithmic bytes.  EINVAL for a
- * bad kind or NULL output. */
+ * (0 <= kind < 24; see trplk_profile_kind_name; kinds 12..23 are the same
+ * families on FP64 data, named with an "_f64" suffix): number of launches,
+ * summed event time in milliseconds and summed algorithmic bytes.  EINVAL
+ * for a bad kind or NULL output. */
 trplk_status trplk_profile_read(trplk_handle* h, int kind, int64_t* launches, double* milliseconds,
                                 double* bytes);
 

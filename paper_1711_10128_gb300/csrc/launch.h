@@ -11,6 +11,11 @@ enum ProfKind : int {
   PK_SPMV = 0, PK_SPMV_SCALED, PK_TS_PROJ, PK_TS_INNER, PK_TS_UPDPROJ, PK_TS_UPDNORM, PK_TS_UPD,
   PK_TS_ROT, PK_TS_RESID, PK_TS_DOT, PK_RR, PK_OTHER, PK_COUNT
 };
+// Families of launches on FP64 data are counted apart from their FP32 twins
+// (kinds PK_COUNT + base): the two bind on different units.
+constexpr int kProfKinds = 2 * PK_COUNT;
+template <typename S>
+constexpr int prof_kind(int base) { return sizeof(S) == 8 ? PK_COUNT + base : base; }
 
 // Counts every kernel launch; when `on`, brackets each launch with CUDA
 // events on the launching stream and records its algorithmic bytes.

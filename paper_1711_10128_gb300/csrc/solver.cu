@@ -957,9 +957,11 @@ trplk_status trplk_check_residuals(trplk_handle* h, const trplk_csr* A, const tr
   });
 }
 
-static const char* kProfNames[PK_COUNT] = {"spmv", "spmv_scaled", "ts_project", "ts_inner", "ts_update_project",
-                                           "ts_update_norm", "ts_update", "ts_rotate", "ts_resid", "ts_dot",
-                                           "rayleigh_ritz", "other"};
+static const char* kProfNames[kProfKinds] = {
+    "spmv", "spmv_scaled", "ts_project", "ts_inner", "ts_update_project", "ts_update_norm", "ts_update",
+    "ts_rotate", "ts_resid", "ts_dot", "rayleigh_ritz", "other",
+    "spmv_f64", "spmv_scaled_f64", "ts_project_f64", "ts_inner_f64", "ts_update_project_f64", "ts_update_norm_f64",
+    "ts_update_f64", "ts_rotate_f64", "ts_resid_f64", "ts_dot_f64", "rayleigh_ritz_f64", "other_f64"};
 
 trplk_status trplk_profile(trplk_handle* h, int enable) {
   return guarded(h, [&]() -> trplk_status {
@@ -971,13 +973,13 @@ trplk_status trplk_profile(trplk_handle* h, int enable) {
 }
 
 const char* trplk_profile_kind_name(int kind) {
-  return (kind >= 0 && kind < PK_COUNT) ? kProfNames[kind] : nullptr;
+  return (kind >= 0 && kind < kProfKinds) ? kProfNames[kind] : nullptr;
 }
 
 trplk_status trplk_profile_read(trplk_handle* h, int kind, int64_t* launches, double* milliseconds,
                                 double* bytes) {
   return guarded(h, [&]() -> trplk_status {
-    if (kind < 0 || kind >= PK_COUNT || !launches || !milliseconds || !bytes)
+    if (kind < 0 || kind >= kProfKinds || !launches || !milliseconds || !bytes)
       throw Error(TRPLK_EINVAL, "bad profile query");
     h->sync();
     int64_t n = 0;

@@ -232,7 +232,7 @@ void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const doubl
     double bytes = (double)A.nnz * (sizeof(S) + 4) + (double)(nslices + 1) * 8 + 2.0 * A.n * sizeof(S);
     if (hyb) bytes += (double)m * 4 + (double)nlong * 20;
     if (scaled) bytes += (double)A.n * sizeof(S) * (bx ? 3 : 1);
-    ProfScope ps(c, scaled ? PK_SPMV_SCALED : PK_SPMV, bytes);
+    ProfScope ps(c, prof_kind<S>(scaled ? PK_SPMV_SCALED : PK_SPMV), bytes);
     const unsigned gb = (unsigned)(blocks > 0 ? blocks : 1);
 #define TRPLK_SELL(SC, HY)                                                                                  \
   sell_spmv_kernel<S, SC, HY><<<gb, 256, 0, c.stream>>>(m, nslices, A.sl_ptr, A.sl_col, A.sl_val, A.sl_perm,  \
@@ -255,7 +255,7 @@ void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const doubl
   // the scaled copies) written once
   double bytes = (double)A.nnz * (sizeof(S) + 4) + (double)(A.n + 1) * 8 + 2.0 * A.n * sizeof(S);
   if (scaled) bytes += (double)A.n * sizeof(S) * (bx ? 3 : 1);
-  ProfScope ps(c, scaled ? PK_SPMV_SCALED : PK_SPMV, bytes);
+  ProfScope ps(c, prof_kind<S>(scaled ? PK_SPMV_SCALED : PK_SPMV), bytes);
   if (scaled) {
     static bool cfg = false;
     if (!cfg) { TRPLK_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); cfg = true; }

@@ -14,9 +14,11 @@
 //  * compute reads shared memory only: thread-per-row for the updates
 //    v <- v - U h, and balanced (column, row-slice) tasks for the projections
 //    U^T v, each task with its own accumulator;
-//  * projections accumulate in FP64 (double data) or Dot2-compensated FP32
-//    (float data) -- except the first CGS pass of the float path, accumulated
-//    plainly in FP32 because the second, compensated pass removes its error --
+//  * projections accumulate in FP64 (double data) or compensated FP32 (float
+//    data: each lane's four consecutive products summed in FP32, the block
+//    sums added exactly by TwoSum) -- except the first CGS pass of the float
+//    path, accumulated plainly in FP32 because the second, compensated pass
+//    removes its error --
 //    are reduced per CTA and then summed in CTA order by the last CTA to
 //    finish (deterministic, no floating-point atomics).
 // Rows n..ld-1 of every array are zero, so whole tiles are always copied.
@@ -301,14 +303,8 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
           const V4<S> u = ld4(m0 + off);
           const V4<S> u2 = ld4(m0 + off2);
           if (KIND == TS_PROJ) {
-            acc0[j].fma(u.x, z.x);
-            if (two) acc0[j + 1].fma(u2.x, z2.x);
-            acc0[j].fma(u.y, z.y);
-            if (two) acc0[j + 1].fma(u2.y, z2.y);
-            acc0[j].fma(u.z, z.z);
-            if (two) acc0[j + 1].fma(u2.z, z2.z);
-            acc0[j].fma(u.w, z.w);
-            if (two) acc0[j + 1].fma(u2.w, z2.w);
+            acc0[j].fma4(u.x, z.x, u.y, z.y, u.z, z.z, u.w, z.w);
+            if (two) acc0[j + 1].fma4(u2.x, z2.x, u2.y, z2.y, u2.z, z2.z, u2.w, z2.w);
             continue;
           }
           if (KIND == TS_INNER) {
@@ -316,22 +312,12 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
             const V4<S> v2 = (NQ == 1 || h2 == 0) ? vq[0] : vq[NQ - 1];
             const V4<S> b = alias ? u : ld4(m1 + off);
             const V4<S> b2 = alias ? u2 : ld4(m1 + off2);
-            acc0[j].fma(u.x, z.x);
-            acc1[j].fma(b.x, v.x);
-            if (two) acc0[j + 1].fma(u2.x, z2.x);
-            if (two) acc1[j + 1].fma(b2.x, v2.x);
-            acc0[j].fma(u.y, z.y);
-            acc1[j].fma(b.y, v.y);
-            if (two) acc0[j + 1].fma(u2.y, z2.y);
-            if (two) acc1[j + 1].fma(b2.y, v2.y);
-            acc0[j].fma(u.z, z.z);
-            acc1[j].fma(b.z, v.z);
-            if (two) acc0[j + 1].fma(u2.z, z2.z);
-            if (two) acc1[j + 1].fma(b2.z, v2.z);
-            acc0[j].fma(u.w, z.w);
-            acc1[j].fma(b.w, v.w);
-            if (two) acc0[j + 1].fma(u2.w, z2.w);
-            if (two) acc1[j + 1].fma(b2.w, v2.w);
+            acc0[j].fma4(u.x, z.x, u.y, z.y, u.z, z.z, u.w, z.w);
+            acc1[j].fma4(b.x, v.x, b.y, v.y, b.z, v.z, b.w, v.w);
+            if (two) {
+              acc0[j + 1].fma4(u2.x, z2.x, u2.y, z2.y, u2.z, z2.z, u2.w, z2.w);
+              acc1[j + 1].fma4(b2.x, v2.x, b2.y, v2.y, b2.z, v2.z, b2.w, v2.w);
+            }
             continue;
           }
           {  // TS_RESID: ||AX_c - theta_c BX_c||^2 and ||X_c||^2 (second task handled alone below)
@@ -343,14 +329,8 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
               const S th = s_y[cc];
               const V4<S> ax = ld4(m1 + oo), bx = ld4(m2 + oo);
               const S r0 = ax.x - th * bx.x, r1 = ax.y - th * bx.y, r2 = ax.z - th * bx.z, r3 = ax.w - th * bx.w;
-              acc0[j + q].fma(r0, r0);
-              acc1[j + q].fma(uu.x, uu.x);
-              acc0[j + q].fma(r1, r1);
-              acc1[j + q].fma(uu.y, uu.y);
-              acc0[j + q].fma(r2, r2);
-              acc1[j + q].fma(uu.z, uu.z);
-              acc0[j + q].fma(r3, r3);
-              acc1[j + q].fma(uu.w, uu.w);
+              acc0[j + q].fma4(r0, r0, r1, r1, r2, r2, r3, r3);
+              acc1[j + q].fma4(uu.x, uu.x, uu.y, uu.y, uu.z, uu.z, uu.w, uu.w);
             }
           }
         }
@@ -384,14 +364,8 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
             const V4<S> b2 = ld4(m1 + cc2 * TR + h2 * SLICE + 4 * lane);
             const V4<S> v = (NQ == 1 || h == 0) ? vq[0] : vq[NQ - 1];
             const V4<S> v2 = (NQ == 1 || h2 == 0) ? vq[0] : vq[NQ - 1];
-            acc0[j].fma(b.x, v.x);
-            if (two) acc0[j + 1].fma(b2.x, v2.x);
-            acc0[j].fma(b.y, v.y);
-            if (two) acc0[j + 1].fma(b2.y, v2.y);
-            acc0[j].fma(b.z, v.z);
-            if (two) acc0[j + 1].fma(b2.z, v2.z);
-            acc0[j].fma(b.w, v.w);
-            if (two) acc0[j + 1].fma(b2.w, v2.w);
+            acc0[j].fma4(b.x, v.x, b.y, v.y, b.z, v.z, b.w, v.w);
+            if (two) acc0[j + 1].fma4(b2.x, v2.x, b2.y, v2.y, b2.z, v2.z, b2.w, v2.w);
           }
         }
       } else if (KIND == TS_ROT) {
