@@ -1,21 +1,25 @@
 // Rayleigh-Ritz eigensolver for the small projection T (Algorithm 1,
 // 'compute eigenpairs of T, T = Y Theta Y^T').
 //
-// One CTA, T (w <= 64) in shared memory.  The cyclic Jacobi method with the
-// round-robin (tournament) ordering: each round rotates w/2 disjoint index
-// pairs at once -- three parallel phases (rotation angles, column updates
-// A J and V J, row updates J^T A) -- and w - 1 rounds make a sweep over all
-// pairs.  Rotations use the symmetric 2x2 Schur decomposition of Golub and
-// Van Loan (Sec. 8.5); the rotated pair's off-diagonal entry is set to zero.
-// Off-diagonal norms are summed directly, never as a difference of norms.
+// One CTA, T (w <= 64) in shared memory, padded to an even order wp with a
+// zero row and column.  The cyclic Jacobi method with the round-robin
+// (tournament) ordering: each round rotates the wp/2 disjoint index pairs at
+// once.  Rotations use the symmetric 2x2 Schur decomposition of Golub and Van
+// Loan (Sec. 8.5).  A round is two phases: the rotation angles, then the
+// similarity A <- J^T A J applied block by block -- the 2x2 block of rows
+// (p_K, q_K) and columns (p_L, q_L) becomes R_K^T A_KL R_L, each block (and its
+// mirror) owned by one thread -- together with V <- V J.  The rotated pairs'
+// off-diagonal entries are set to zero.  Off-diagonal norms are summed
+// directly, never as a difference of norms.
 //
 // The FP64 pipe of this GPU retires 2 FMAs per clock per SM (the FP32 pipe
 // 128), so the sweeps run in two precisions:
 //  1. FP32 sweeps on fp32(T) until its off-diagonal norm is <= 1e-6 ||T||_F,
 //     accumulating the rotations into V (orthogonal to about 1e-7);
-//  2. V is promoted to FP64 and re-orthonormalised by two Gram-Schmidt passes
-//     per column, then B = V^T T V is formed in FP64 (an exact orthogonal
-//     similarity up to FP64 rounding) -- nearly diagonal;
+//  2. V is promoted to FP64 and made orthogonal to FP64 rounding by two
+//     Newton-Schulz steps V <- V (3 I - V^T V) / 2 (each squares the
+//     departure from orthogonality), then B = V^T T V is formed in FP64 (an
+//     orthogonal similarity up to FP64 rounding) -- nearly diagonal;
 //  3. FP64 sweeps on B (quadratic convergence: usually one or two) until its
 //     off-diagonal norm is <= 1e-15 ||T||_F, accumulating into V.
 // Eigenvalues are then sorted ascending (stable rank sort) and every
@@ -30,6 +34,8 @@ namespace trplk {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kMaxPairs = kMaxQ / 2;
+constexpr int kMaxBlocks = kMaxPairs * (kMaxPairs + 1) / 2;
 
 template <typename T>
 __device__ __forceinline__ void sym_schur2(T app, T aqq, T apq, T skip, T& c, T& s) {
@@ -45,11 +51,20 @@ __device__ __forceinline__ void sym_schur2(T app, T aqq, T apq, T skip, T& c, T&
 }
 
 struct RotShared {
-  int p[kMaxQ / 2], q[kMaxQ / 2];
-  double c[kMaxQ / 2], s[kMaxQ / 2];
+  int p[kMaxPairs], q[kMaxPairs];
+  double c[kMaxPairs], s[kMaxPairs];
+  float cf[kMaxPairs], sf[kMaxPairs];
+  unsigned char bk[kMaxBlocks], bl[kMaxBlocks];   // block b -> pairs (K, L), K <= L
   double red[kThreads / 32];
   double val;
 };
+
+template <typename T> __device__ __forceinline__ T rot_c(const RotShared& sh, int k);
+template <> __device__ __forceinline__ double rot_c<double>(const RotShared& sh, int k) { return sh.c[k]; }
+template <> __device__ __forceinline__ float rot_c<float>(const RotShared& sh, int k) { return sh.cf[k]; }
+template <typename T> __device__ __forceinline__ T rot_s(const RotShared& sh, int k);
+template <> __device__ __forceinline__ double rot_s<double>(const RotShared& sh, int k) { return sh.s[k]; }
+template <> __device__ __forceinline__ float rot_s<float>(const RotShared& sh, int k) { return sh.sf[k]; }
 
 // sum over the CTA; result valid in every thread
 __device__ double block_sum(double v, RotShared& sh) {
@@ -79,61 +94,72 @@ __device__ double off_norm(const T* A, int w, int ld, RotShared& sh) {
   return sqrt(block_sum(o, sh));
 }
 
-// Jacobi sweeps on the symmetric A (row-major, ld), rotations accumulated into
-// V.  Stops when the off-diagonal norm is <= tol * fro.  Returns true if it did.
+// Jacobi sweeps on the symmetric A (wp x wp, row-major, ld, zero beyond w),
+// rotations accumulated into V.  Stops when the off-diagonal norm is
+// <= tol * fro.  Returns true if it did.
 template <typename T>
-__device__ bool jacobi_sweeps(T* A, T* V, int w, int ld, double fro, double tol, double skip_rel, int max_sweeps,
-                              RotShared& sh) {
+__device__ bool jacobi_sweeps(T* A, T* V, int w, int wp, int ld, double fro, double tol, double skip_rel,
+                              int max_sweeps, RotShared& sh) {
   const int tid = threadIdx.x;
-  const int wp = w + (w & 1);   // even number of slots; slot w (if any) is a dummy
   const int npairs = wp / 2;
+  const int nblk = npairs * (npairs + 1) / 2;
+  const int ntask = nblk + npairs * w;   // A blocks, then (row of V, pair) tasks
   const T skip = (T)(skip_rel * fro);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (off_norm(A, w, ld, sh) <= tol * fro) return true;
     for (int round = 0; round < wp - 1; ++round) {
       if (tid < npairs) {
         // tournament ordering: slot 0 fixed, slots 1..wp-1 rotate
-        auto slot = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + round) % (wp - 1); };
-        int p = slot(tid), q = slot(wp - 1 - tid);
+        int p = tid == 0 ? 0 : 1 + (tid - 1 + round) % (wp - 1);
+        int q = 1 + (wp - 2 - tid + round) % (wp - 1);
         if (p > q) { const int tmp = p; p = q; q = tmp; }
         T c = 1, s = 0;
-        if (q < w) sym_schur2<T>(A[p * ld + p], A[q * ld + q], A[p * ld + q], skip, c, s);
+        sym_schur2<T>(A[p * ld + p], A[q * ld + q], A[p * ld + q], skip, c, s);
         sh.p[tid] = p;
         sh.q[tid] = q;
-        sh.c[tid] = (double)c;
-        sh.s[tid] = (double)s;
+        if (sizeof(T) == 8) { sh.c[tid] = (double)c; sh.s[tid] = (double)s; }
+        else { sh.cf[tid] = (float)c; sh.sf[tid] = (float)s; }
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int e = tid; e < npairs * w; e += kThreads) {
-        const int k = e / w, i = e - k * w;
-        const T s = (T)sh.s[k];
-        if (s == 0) continue;
-        const T c = (T)sh.c[k];
-        const int p = sh.p[k], q = sh.q[k];
-        const T aip = A[i * ld + p], aiq = A[i * ld + q];
-        A[i * ld + p] = c * aip - s * aiq;
-        A[i * ld + q] = s * aip + c * aiq;
-        const T vip = V[i * ld + p], viq = V[i * ld + q];
-        V[i * ld + p] = c * vip - s * viq;
-        V[i * ld + q] = s * vip + c * viq;
-      }
-      __syncthreads();
-      // rows: A <- J^T A
-      for (int e = tid; e < npairs * w; e += kThreads) {
-        const int k = e / w, j = e - k * w;
-        const T s = (T)sh.s[k];
-        if (s == 0) continue;
-        const T c = (T)sh.c[k];
-        const int p = sh.p[k], q = sh.q[k];
-        const T apj = A[p * ld + j], aqj = A[q * ld + j];
-        A[p * ld + j] = c * apj - s * aqj;
-        A[q * ld + j] = s * apj + c * aqj;
-      }
-      __syncthreads();
-      if (tid < npairs && sh.s[tid] != 0.0) {
-        A[sh.p[tid] * ld + sh.q[tid]] = 0;
-        A[sh.q[tid] * ld + sh.p[tid]] = 0;
+      for (int t = tid; t < ntask; t += kThreads) {
+        if (t < nblk) {
+          const int K = sh.bk[t], L = sh.bl[t];
+          const T sK = rot_s<T>(sh, K), sL = rot_s<T>(sh, L);
+          if (sK == 0 && sL == 0) continue;
+          const T cK = rot_c<T>(sh, K), cL = rot_c<T>(sh, L);
+          const int pK = sh.p[K], qK = sh.q[K], pL = sh.p[L], qL = sh.q[L];
+          const T x00 = A[pK * ld + pL], x01 = A[pK * ld + qL], x10 = A[qK * ld + pL], x11 = A[qK * ld + qL];
+          // Y = X R_L (columns), Z = R_K^T Y (rows)
+          const T y00 = cL * x00 - sL * x01, y01 = sL * x00 + cL * x01;
+          const T y10 = cL * x10 - sL * x11, y11 = sL * x10 + cL * x11;
+          const T z00 = cK * y00 - sK * y10, z10 = sK * y00 + cK * y10;
+          const T z01 = cK * y01 - sK * y11, z11 = sK * y01 + cK * y11;
+          if (K == L) {
+            A[pK * ld + pK] = z00;
+            A[qK * ld + qK] = z11;
+            A[pK * ld + qK] = 0;
+            A[qK * ld + pK] = 0;
+          } else {
+            A[pK * ld + pL] = z00;
+            A[pK * ld + qL] = z01;
+            A[qK * ld + pL] = z10;
+            A[qK * ld + qL] = z11;
+            A[pL * ld + pK] = z00;
+            A[qL * ld + pK] = z01;
+            A[pL * ld + qK] = z10;
+            A[qL * ld + qK] = z11;
+          }
+        } else {
+          const int e = t - nblk;
+          const int L = e / w, i = e - L * w;
+          const T sL = rot_s<T>(sh, L);
+          if (sL == 0) continue;
+          const T cL = rot_c<T>(sh, L);
+          const int pL = sh.p[L], qL = sh.q[L];
+          const T vp = V[i * ld + pL], vq = V[i * ld + qL];
+          V[i * ld + pL] = cL * vp - sL * vq;
+          V[i * ld + qL] = sL * vp + cL * vq;
+        }
       }
       __syncthreads();
     }
@@ -141,26 +167,55 @@ __device__ bool jacobi_sweeps(T* A, T* V, int w, int ld, double fro, double tol,
   return off_norm(A, w, ld, sh) <= tol * fro;
 }
 
+// X = V (3 I - V^T V) / 2 for the w x w V (FP64); M, X scratch.
+__device__ void newton_schulz(const double* V, double* M, double* X, int w, int ld) {
+  for (int e = threadIdx.x; e < w * w; e += kThreads) {
+    const int i = e / w, j = e - i * w;
+    double s = 0.0;
+    for (int r = 0; r < w; ++r) s = fma(V[r * ld + i], V[r * ld + j], s);
+    M[i * ld + j] = (i == j ? 1.5 : 0.0) - 0.5 * s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < w * w; e += kThreads) {
+    const int i = e / w, j = e - i * w;
+    double s = 0.0;
+    for (int r = 0; r < w; ++r) s = fma(V[i * ld + r], M[r * ld + j], s);
+    X[i * ld + j] = s;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kThreads) rr_kernel(int w, const double* __restrict__ T, int ldT,
                                                       double* __restrict__ theta, double* __restrict__ Y, int* status) {
   extern __shared__ __align__(16) double sh_d[];
   __shared__ RotShared sh;
   __shared__ int s_rank[kMaxQ];
-  const int ld = w + 1;   // padded rows (bank spread)
+  const int wp = w + (w & 1);   // even order; index w (if any) is a zero dummy
+  const int ld = wp + 1;        // padded rows (bank spread)
   double* A = sh_d;                       // T, then B = V^T T V (FP64)
-  double* V = A + w * ld;                 // eigenvectors (FP64)
-  double* W = V + w * ld;                 // scratch (FP64): T V
-  float* A32 = reinterpret_cast<float*>(W + w * ld);
-  float* V32 = A32 + w * ld;
+  double* V = A + wp * ld;                // eigenvectors (FP64)
+  double* W = V + wp * ld;                // scratch (FP64)
+  double* X = W + wp * ld;                // scratch (FP64)
+  float* A32 = reinterpret_cast<float*>(X + wp * ld);
+  float* V32 = A32 + wp * ld;
   const int tid = threadIdx.x;
 
-  for (int e = tid; e < w * w; e += kThreads) {
-    const int i = e / w, j = e - i * w;
+  for (int e = tid; e < wp * wp; e += kThreads) {
+    const int i = e / wp, j = e - i * wp;
     const int r = i < j ? i : j, cc = i < j ? j : i;
-    const double a = T[(int64_t)cc * ldT + r];
+    const double a = (i < w && j < w) ? T[(int64_t)cc * ldT + r] : 0.0;
     A[i * ld + j] = a;
     A32[i * ld + j] = (float)a;
-    V32[i * ld + j] = (i == j) ? 1.f : 0.f;
+    V32[i * ld + j] = (i == j && i < w) ? 1.f : 0.f;
+  }
+  {
+    const int np = wp / 2;
+    for (int b = tid; b < np * (np + 1) / 2; b += kThreads) {
+      int K = 0, rem = b;   // row K of the upper triangle holds np - K blocks
+      while (rem >= np - K) { rem -= np - K; ++K; }
+      sh.bk[b] = (unsigned char)K;
+      sh.bl[b] = (unsigned char)(K + rem);
+    }
   }
   __syncthreads();
   double f = 0.0;
@@ -173,38 +228,17 @@ __global__ void __launch_bounds__(kThreads) rr_kernel(int w, const double* __res
   bool ok = true;
   if (w > 1 && fro > 0.0) {
     // 1. FP32 sweeps
-    jacobi_sweeps<float>(A32, V32, w, ld, fro, 1e-6, 1e-9, 20, sh);
-    // 2. promote V, re-orthonormalise (two Gram-Schmidt passes per column)
-    for (int e = tid; e < w * w; e += kThreads) V[(e / w) * ld + (e % w)] = (double)V32[(e / w) * ld + (e % w)];
+    jacobi_sweeps<float>(A32, V32, w, wp, ld, fro, 1e-6, 1e-9, 20, sh);
+    // 2. promote V, two Newton-Schulz steps (V <-> X ping-pong)
+    for (int e = tid; e < wp * wp; e += kThreads) V[(e / wp) * ld + (e % wp)] = (double)V32[(e / wp) * ld + (e % wp)];
     __syncthreads();
-    for (int j = 0; j < w; ++j) {
-      for (int pass = 0; pass < 2; ++pass) {
-        // h_i = V[:, i] . V[:, j] for i < j, one warp per coefficient
-        for (int i = tid >> 5; i < j; i += kThreads / 32) {
-          double d = 0.0;
-          for (int r = tid & 31; r < w; r += 32) d += V[r * ld + i] * V[r * ld + j];
-          for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
-          if ((tid & 31) == 0) W[i] = d;
-        }
-        __syncthreads();
-        for (int r = tid; r < w; r += kThreads) {
-          double s = 0.0;
-          for (int i = 0; i < j; ++i) s += V[r * ld + i] * W[i];
-          V[r * ld + j] -= s;
-        }
-        __syncthreads();
-      }
-      double nn = 0.0;
-      for (int r = tid; r < w; r += kThreads) nn += V[r * ld + j] * V[r * ld + j];
-      const double inv = 1.0 / sqrt(block_sum(nn, sh));
-      for (int r = tid; r < w; r += kThreads) V[r * ld + j] *= inv;
-      __syncthreads();
-    }
+    newton_schulz(V, W, X, w, ld);
+    newton_schulz(X, W, V, w, ld);
     // 3. B = V^T T V in FP64 (W = T V, then A = V^T W)
     for (int e = tid; e < w * w; e += kThreads) {
       const int i = e / w, j = e - i * w;
       double s = 0.0;
-      for (int r = 0; r < w; ++r) s += A[i * ld + r] * V[r * ld + j];
+      for (int r = 0; r < w; ++r) s = fma(A[i * ld + r], V[r * ld + j], s);
       W[i * ld + j] = s;
     }
     __syncthreads();
@@ -212,13 +246,13 @@ __global__ void __launch_bounds__(kThreads) rr_kernel(int w, const double* __res
       const int i = e / w, j = e - i * w;
       if (j < i) continue;
       double s = 0.0;
-      for (int r = 0; r < w; ++r) s += V[r * ld + i] * W[r * ld + j];
+      for (int r = 0; r < w; ++r) s = fma(V[r * ld + i], W[r * ld + j], s);
       A[i * ld + j] = s;
       A[j * ld + i] = s;
     }
     __syncthreads();
     // 4. FP64 polishing sweeps
-    ok = jacobi_sweeps<double>(A, V, w, ld, fro, 1e-15, 1e-18, 30, sh);
+    ok = jacobi_sweeps<double>(A, V, w, wp, ld, fro, 1e-15, 1e-18, 30, sh);
   } else if (w == 1) {
     if (tid == 0) V[0] = 1.0;
     __syncthreads();
@@ -259,7 +293,10 @@ __global__ void __launch_bounds__(kThreads) rr_kernel(int w, const double* __res
 
 void rayleigh_ritz(const Ctx& c, int w, const double* T, int ldT, double* theta, double* Y) {
   if (w < 1 || w > kMaxQ) throw Error(TRPLK_EINVAL, "Rayleigh-Ritz size out of range");
-  auto bytes = [](int ww) { return (size_t)ww * (ww + 1) * (3 * sizeof(double) + 2 * sizeof(float)); };
+  auto bytes = [](int ww) {
+    const size_t wp = (size_t)(ww + (ww & 1));
+    return wp * (wp + 1) * (4 * sizeof(double) + 2 * sizeof(float));
+  };
   static bool cfg = false;
   if (!cfg) {
     TRPLK_CUDA_TRY(cudaFuncSetAttribute(rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes(kMaxQ)));
