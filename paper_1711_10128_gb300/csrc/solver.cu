@@ -130,6 +130,7 @@ namespace {
 constexpr double kEpsBreakdown64 = 1e-12;
 constexpr double kEpsBreakdown32 = 1e-5;
 constexpr double kEpsDependent = 1e-10;
+constexpr double kBlockNear = 100.0;  // refinement block: pairs within this factor of tol
 
 trplk_status status_from_flags(int f) {
   if (f & kFlagTimeout) return TRPLK_ETIMEOUT;
@@ -274,6 +275,7 @@ struct Solver {
   bool hasB;
   bool skip_converged;          // refinement phase: targets skip converged pairs
   bool check_start = false;     // replace dependent start columns (refinement phase)
+  bool block_refine = false;    // refinement phase: cycles start from all unconverged residuals
   int stall_window = 0;         // >0: stop when the target residual stagnates
   bool stalled = false;
   double* tmp64 = nullptr;
@@ -352,6 +354,16 @@ struct Solver {
       ts_dot_norm<S>(c, ld, v, bv, h1, h2, w, betas + 2 * slot, scale, eps_breakdown);
     } else {
       ts_update_norm<S>(c, ld, w, U[cur], h2, h1, v, betas + 2 * slot, scale, eps_breakdown);
+    }
+  }
+
+  // v = M (A x_i - theta_i B x_i) from the stored images (Algorithm 1, restart)
+  void precond_residual(int cur, int i) {
+    if (MG) {
+      restart_vector<S>(c, ld, col(AU[cur], i), col(BU[cur], i), theta + i, nullptr, PM_IDENTITY, rtmp);
+      apply_fsai(rtmp, v);
+    } else {
+      restart_vector<S>(c, ld, col(AU[cur], i), col(BU[cur], i), theta + i, dinv, pmode, v);
     }
   }
 
@@ -438,8 +450,9 @@ struct Solver {
       return cv;
     };
     int t = 0;
+    std::vector<char> cvec = converged_vec(r, x);
     if (skip_converged) {
-      auto cv = converged_vec(r, x);
+      const auto& cv = cvec;
       while (t < p && cv[t]) ++t;
       if (t >= p) {
         out.converged = true;
@@ -462,19 +475,40 @@ struct Solver {
         set_diag_block_kernel<<<1, 256, 0, c.stream>>>(T, ldT, k, theta);
       }
       check_launch("set_diag_block");
-      // first Lanczos vector u = M (A x_t - rho B x_t)  (Algorithm 1, restart)
-      if (MG) {
-        restart_vector<S>(c, ld, col(AU[cur], t), col(BU[cur], t), theta + t, nullptr, PM_IDENTITY, rtmp);
-        apply_fsai(rtmp, v);
-      } else {
-        restart_vector<S>(c, ld, col(AU[cur], t), col(BU[cur], t), theta + t, dinv, pmode, v);
-      }
-      out.prec++;
-      ts_project<S>(c, ld, k, BU[cur], v, h1);
-      orthonormalize_tail(cur, k, 0, out);
       const int nprev = (xp_buf >= 0) ? xp_count : 0;
-      const int m = q - k - nprev;
-      int w = k;
+      // refinement: first the preconditioned residuals of the other
+      // unconverged pairs already near tol (relative residual <= kBlockNear
+      // tol), each B-orthonormalised against the basis (a block Davidson step
+      // for all of them), dropped when dependent; pairs further away wait for
+      // their turn as the target, whose Krylov steps converge them faster
+      int w0 = k;
+      if (block_refine) {
+        std::vector<int> blk;
+        for (int i = 0; i < p; ++i)
+          if (i != t && !cvec[i] && r[i] <= kBlockNear * tol * normA * x[i]) blk.push_back(i);
+        const int room = std::max(0, q - k - nprev - 1);
+        if ((int)blk.size() > room) blk.resize(room);
+        for (int i : blk) {
+          precond_residual(cur, i);
+          out.prec++;
+          ts_project<S>(c, ld, w0, BU[cur], v, h1);
+          orthonormalize_tail(cur, w0, kMaxQ, out);
+          double* hp = h->host(2);
+          TRPLK_CUDA_TRY(cudaMemcpyAsync(hp, betas + 2 * kMaxQ, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+          h->sync();
+          if (!(hp[0] > eps_breakdown * hp[1])) continue;
+          append(cur, w0, out);
+          ++w0;
+          ts_project<S>(c, ld, w0, U[cur], col(AU[cur], w0 - 1), T + (size_t)(w0 - 1) * ldT);
+        }
+      }
+      // first Lanczos vector u = M (A x_t - rho B x_t)  (Algorithm 1, restart)
+      precond_residual(cur, t);
+      out.prec++;
+      ts_project<S>(c, ld, w0, BU[cur], v, h1);
+      orthonormalize_tail(cur, w0, 0, out);
+      const int m = q - w0 - nprev;
+      int w = w0;
       // inner preconditioned Lanczos with the T update (eq. (UpdateT))
       for (int j = 0; j < m; ++j) {
         append(cur, w, out);
@@ -505,8 +539,8 @@ struct Solver {
           if (!(hp[2 * j] > eps_breakdown * hp[2 * j + 1])) { good = j; break; }
         if (good < m) {
           out.breakdown = true;
-          w = k + good;
-          if (good == 0 && nprev == 0) {
+          w = w0 + good;
+          if (good == 0 && nprev == 0 && w0 == k) {
             out.theta = th;
             out.cur = cur;
             return out;
@@ -533,7 +567,8 @@ struct Solver {
       cur = rr_and_restart(cur, w);
       read_back(k, th, r, x, nullptr, 0);
       check_flags(h, kFlagBreakdown);
-      auto cv = converged_vec(r, x);
+      cvec = converged_vec(r, x);
+      const auto& cv = cvec;
       if (stall_window > 0) {
         // the target's relative residual, tracked while the target is unchanged
         const double rel = r[t] / (normA * x[t]);
@@ -749,15 +784,18 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
       // promote the k Ritz vectors and refine in FP64 from them
       double* Xr = static_cast<double*>(h->get("Xrefine", (size_t)ld * P->k * sizeof(double)));
       convert<double, float>(c, (int64_t)ld * P->k, S32.U[r32.cur], Xr);
-      // The refinement only lifts pairs from about 3e-8 to tol, so it runs with
-      // a smaller basis, q_ref = p_hat + max(l + 2, (q - p_hat) / 5): cycles
-      // are cheaper and more of them advance targets (measured on the 128^3
-      // diffusion operator: 1.22 s at q_ref = q, 1.06 s at q_ref = 18..22).
-      const int q_ref = std::min(P->q, P->k + std::max(P->l + 2, (P->q - P->k) / 5));
+      // The refinement only lifts pairs from about 3e-8 to tol.  Each of its
+      // cycles starts from the preconditioned residuals of all unconverged
+      // pairs (a block step for every pair at once), then kRefineKrylov
+      // Krylov steps on the target, so its basis is
+      // q_ref = p_hat + (p - 1) + 1 + kRefineKrylov + l, at most q.
+      constexpr int kRefineKrylov = 4;
+      const int q_ref = std::min(P->q, P->k + P->p + kRefineKrylov + P->l);
       Solver<double> S64(h, "f64", n, P->p, q_ref, P->k, P->l, P->tol, std::max(1, P->max_cycles - r32.cycles), Aop,
                          Bop, hasB, dinv64, pmode);
       S64.skip_converged = true;
       S64.check_start = true;
+      S64.block_refine = true;
       if (fsai.ok) { S64.MG = &fsai.G; S64.MGT = &fsai.GT; }
       SolveOut r64 = S64.run(Xr);
       inf.cycles = r32.cycles;
