@@ -111,7 +111,6 @@ struct TSLayout {
   static constexpr int NW = TR / 32;              // consumer warps
   static constexpr int NQ = Slices<S>::NQ;
   static constexpr int RPS = TR / (32 * NQ);      // rows per lane per task (4)
-  static constexpr int MAXT = NQ * kMaxQ / NW;    // tasks per warp (upper bound)
   static constexpr uint32_t COLB = TR * sizeof(S);
 };
 
@@ -166,10 +165,14 @@ __device__ __forceinline__ void consumer_sync() {
 template <typename S> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<float> { static constexpr int value = 2; };
 
-template <typename S, int KIND>
+// MAXW: the widest basis the instantiation serves; its accumulators (MAXT
+// tasks per warp) live in registers for the whole kernel, so narrow bases get
+// their own instantiation with a third of them (no spills, see the launcher).
+template <typename S, int KIND, int MAXW = kMaxQ>
 __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kernel(TSArgs<S> a) {
   using L = TSLayout<S>;
-  constexpr int TR = L::TR, NW = L::NW, NQ = L::NQ, RPS = L::RPS, MAXT = L::MAXT;
+  constexpr int TR = L::TR, NW = L::NW, NQ = L::NQ, RPS = L::RPS;
+  constexpr int MAXT = NQ * MAXW / NW;
   constexpr int SLICE = TR / NQ;
   static_assert(RPS == 4, "the task phase maps four consecutive rows to a lane");
   constexpr bool TASKS = (KIND == TS_PROJ || KIND == TS_INNER || KIND == TS_UPDPROJ || KIND == TS_RESID);

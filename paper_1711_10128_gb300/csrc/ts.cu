@@ -13,28 +13,28 @@ constexpr size_t kSmemMax = 232448 - 1024;   // opt-in shared memory per CTA les
 constexpr size_t kSmemPerSM = 233472;        // shared memory per SM
 
 // CTAs of one instantiation that fit on an SM by registers and threads.
-template <typename S, int KIND>
+template <typename S, int KIND, int MAXW>
 int regs_limit() {
   static int lim = 0;
   if (!lim) {
     cudaFuncAttributes fa;
-    TRPLK_CUDA_TRY(cudaFuncGetAttributes(&fa, ts_kernel<S, KIND>));
+    TRPLK_CUDA_TRY(cudaFuncGetAttributes(&fa, ts_kernel<S, KIND, MAXW>));
     const int threads = Tile<S>::TR + 32;
     const int regs = std::max(fa.numRegs, 1) * threads;
     lim = std::max(1, std::min(65536 / regs, 2048 / threads));
-    TRPLK_CUDA_TRY(cudaFuncSetAttribute(ts_kernel<S, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    TRPLK_CUDA_TRY(cudaFuncSetAttribute(ts_kernel<S, KIND, MAXW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)kSmemMax));
   }
   return lim;
 }
 
-template <typename S, int KIND>
+template <typename S, int KIND, int MAXW>
 void launch_kind(const Ctx& c, TSArgs<S>& a, size_t fixed, size_t stage, double bytes) {
   // Most CTAs per SM that still keep >= 2 stages each (measured: a second
   // producer/consumer group per SM hides more latency than deeper pipelines
   // of one group, e.g. 56.7 us against 87.5 us for the FP32 update+norm pass
   // at n = 2^21, w = 32), then as many stages as fit, up to 8.
-  const int lim = regs_limit<S, KIND>();
+  const int lim = regs_limit<S, KIND, MAXW>();
   int per_sm = 1, stages = 0;
   for (int cand = lim; cand >= 1; --cand) {
     const size_t per_cta = std::min<size_t>(kSmemMax, kSmemPerSM / cand - 1024);
@@ -52,8 +52,21 @@ void launch_kind(const Ctx& c, TSArgs<S>& a, size_t fixed, size_t stage, double 
   int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)c.sms * per_sm);
   grid = std::min(grid, kMaxPartials);
   ProfScope ps(c, prof_kind<S>(PK_TS_PROJ + KIND), bytes);
-  ts_kernel<S, KIND><<<grid, Tile<S>::TR + 32, smem, c.stream>>>(a);
+  ts_kernel<S, KIND, MAXW><<<grid, Tile<S>::TR + 32, smem, c.stream>>>(a);
   check_launch("ts_kernel");
+}
+
+// Kinds with per-warp projection tasks get instantiations sized for the
+// basis width (w <= 32, <= 48, <= 64): the accumulators of the widest one
+// spilled inside its task loop (measured at w = 23).
+template <typename S, int KIND>
+void launch_tasks(const Ctx& c, TSArgs<S>& a, size_t fixed, size_t stage, double bytes) {
+  if (a.w <= kMaxQ / 2)
+    launch_kind<S, KIND, kMaxQ / 2>(c, a, fixed, stage, bytes);
+  else if (a.w <= 3 * kMaxQ / 4)
+    launch_kind<S, KIND, 3 * kMaxQ / 4>(c, a, fixed, stage, bytes);
+  else
+    launch_kind<S, KIND, kMaxQ>(c, a, fixed, stage, bytes);
 }
 
 template <typename S>
@@ -76,14 +89,14 @@ void run(const Ctx& c, TSArgs<S> a, int kind) {
   if (kind == TS_UPDPROJ || kind == TS_UPDNORM || kind == TS_UPD) bytes += (double)a.ld * sizeof(S);
   if (kind == TS_ROT) bytes += (double)a.k * a.ld * sizeof(S);
   switch (kind) {
-    case TS_PROJ: launch_kind<S, TS_PROJ>(c, a, fixed, stage, bytes); break;
-    case TS_INNER: launch_kind<S, TS_INNER>(c, a, fixed, stage, bytes); break;
-    case TS_UPDPROJ: launch_kind<S, TS_UPDPROJ>(c, a, fixed, stage, bytes); break;
-    case TS_UPDNORM: launch_kind<S, TS_UPDNORM>(c, a, fixed, stage, bytes); break;
-    case TS_UPD: launch_kind<S, TS_UPD>(c, a, fixed, stage, bytes); break;
-    case TS_ROT: launch_kind<S, TS_ROT>(c, a, fixed, stage, bytes); break;
-    case TS_RESID: launch_kind<S, TS_RESID>(c, a, fixed, stage, bytes); break;
-    case TS_DOT: launch_kind<S, TS_DOT>(c, a, fixed, stage, bytes); break;
+    case TS_PROJ: launch_tasks<S, TS_PROJ>(c, a, fixed, stage, bytes); break;
+    case TS_INNER: launch_tasks<S, TS_INNER>(c, a, fixed, stage, bytes); break;
+    case TS_UPDPROJ: launch_tasks<S, TS_UPDPROJ>(c, a, fixed, stage, bytes); break;
+    case TS_UPDNORM: launch_kind<S, TS_UPDNORM, kMaxQ>(c, a, fixed, stage, bytes); break;
+    case TS_UPD: launch_kind<S, TS_UPD, kMaxQ>(c, a, fixed, stage, bytes); break;
+    case TS_ROT: launch_kind<S, TS_ROT, kMaxQ>(c, a, fixed, stage, bytes); break;
+    case TS_RESID: launch_tasks<S, TS_RESID>(c, a, fixed, stage, bytes); break;
+    case TS_DOT: launch_kind<S, TS_DOT, kMaxQ>(c, a, fixed, stage, bytes); break;
     default: throw Error(TRPLK_EINVAL, "unknown tall-skinny kind");
   }
 }
