@@ -20,8 +20,9 @@
 //     Newton-Schulz steps V <- V (3 I - V^T V) / 2 (each squares the
 //     departure from orthogonality), then B = V^T T V is formed in FP64 (an
 //     orthogonal similarity up to FP64 rounding) -- nearly diagonal;
-//  3. FP64 sweeps on B (quadratic convergence: usually one or two) until its
-//     off-diagonal norm is <= 1e-15 ||T||_F, accumulating into V.
+//  3. FP64 sweeps on B (quadratic convergence: usually one or two; the second
+//     skips the rotations already below 1e-16 ||T||_F) until its
+//     off-diagonal norm is <= 3e-15 ||T||_F, accumulating into V.
 // Eigenvalues are then sorted ascending (stable rank sort) and every
 // eigenvector is signed so its largest-magnitude entry, the first such, is
 // positive.
@@ -33,7 +34,7 @@ namespace trplk {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kMaxPairs = kMaxQ / 2;
 constexpr int kMaxBlocks = kMaxPairs * (kMaxPairs + 1) / 2;
 
@@ -55,6 +56,7 @@ struct RotShared {
   double c[kMaxPairs], s[kMaxPairs];
   float cf[kMaxPairs], sf[kMaxPairs];
   unsigned char bk[kMaxBlocks], bl[kMaxBlocks];   // block b -> pairs (K, L), K <= L
+  unsigned char sp[kMaxQ - 1][kMaxPairs], sq[kMaxQ - 1][kMaxPairs];   // round -> pair -> (p, q), p < q
   double red[kThreads / 32];
   double val;
 };
@@ -103,16 +105,15 @@ __device__ bool jacobi_sweeps(T* A, T* V, int w, int wp, int ld, double fro, dou
   const int tid = threadIdx.x;
   const int npairs = wp / 2;
   const int nblk = npairs * (npairs + 1) / 2;
-  const int ntask = nblk + npairs * w;   // A blocks, then (row of V, pair) tasks
+  int lgw = 0;   // V tasks: row i = e & (2^lgw - 1), pair L = e >> lgw (rows >= w idle)
+  while ((1 << lgw) < w) ++lgw;
+  const int ntask = nblk + (npairs << lgw);   // A blocks, then (row of V, pair) tasks
   const T skip = (T)(skip_rel * fro);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (off_norm(A, w, ld, sh) <= tol * fro) return true;
     for (int round = 0; round < wp - 1; ++round) {
       if (tid < npairs) {
-        // tournament ordering: slot 0 fixed, slots 1..wp-1 rotate
-        int p = tid == 0 ? 0 : 1 + (tid - 1 + round) % (wp - 1);
-        int q = 1 + (wp - 2 - tid + round) % (wp - 1);
-        if (p > q) { const int tmp = p; p = q; q = tmp; }
+        const int p = sh.sp[round][tid], q = sh.sq[round][tid];
         T c = 1, s = 0;
         sym_schur2<T>(A[p * ld + p], A[q * ld + q], A[p * ld + q], skip, c, s);
         sh.p[tid] = p;
@@ -151,7 +152,8 @@ __device__ bool jacobi_sweeps(T* A, T* V, int w, int wp, int ld, double fro, dou
           }
         } else {
           const int e = t - nblk;
-          const int L = e / w, i = e - L * w;
+          const int L = e >> lgw, i = e & ((1 << lgw) - 1);
+          if (i >= w) continue;
           const T sL = rot_s<T>(sh, L);
           if (sL == 0) continue;
           const T cL = rot_c<T>(sh, L);
@@ -210,6 +212,15 @@ __global__ void __launch_bounds__(kThreads) rr_kernel(int w, const double* __res
   }
   {
     const int np = wp / 2;
+    // tournament ordering: slot 0 fixed, slots 1..wp-1 rotate one place per round
+    for (int e = tid; e < (wp - 1) * np; e += kThreads) {
+      const int round = e / np, k = e - round * np;
+      int p = k == 0 ? 0 : 1 + (k - 1 + round) % (wp - 1);
+      int q = 1 + (wp - 2 - k + round) % (wp - 1);
+      if (p > q) { const int tmp = p; p = q; q = tmp; }
+      sh.sp[round][k] = (unsigned char)p;
+      sh.sq[round][k] = (unsigned char)q;
+    }
     for (int b = tid; b < np * (np + 1) / 2; b += kThreads) {
       int K = 0, rem = b;   // row K of the upper triangle holds np - K blocks
       while (rem >= np - K) { rem -= np - K; ++K; }
@@ -251,8 +262,10 @@ __global__ void __launch_bounds__(kThreads) rr_kernel(int w, const double* __res
       A[j * ld + i] = s;
     }
     __syncthreads();
-    // 4. FP64 polishing sweeps
-    ok = jacobi_sweeps<double>(A, V, w, wp, ld, fro, 1e-15, 1e-18, 30, sh);
+    // 4. FP64 polishing sweeps.  Rotations with |a_pq| <= 1e-16 ||T||_F are
+    // skipped (their effect on eigenvalues is below a_pq^2 / gap), so the
+    // stopping norm is 3e-15 ||T||_F >= sqrt(w^2 / 2) * 1e-16 ||T||_F.
+    ok = jacobi_sweeps<double>(A, V, w, wp, ld, fro, 3e-15, 1e-16, 30, sh);
   } else if (w == 1) {
     if (tid == 0) V[0] = 1.0;
     __syncthreads();
