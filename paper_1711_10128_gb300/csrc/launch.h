@@ -107,8 +107,18 @@ struct DevCsr {
   int64_t sl_rows = 0;               // rows in the SELL part (n without sl_perm)
   const int32_t* long_rows = nullptr;
   int64_t n_long_cta = 0, n_long_warp = 0;
+  // optional diagonal (DIA) copy for operators whose entries lie on at most
+  // kMaxDiag diagonals (stencils, structured FEM): values dia_val[d * ld + i]
+  // of a_{i, i + dia_off[d]} (zero where absent), ld = n rounded up to 256;
+  // used by the matvec when present (no column indices to read)
+  const S* dia_val = nullptr;
+  int64_t dia_ld = 0;
+  int ndiag = 0;
+  int dia_off[64] = {};
 };
 
+constexpr int kMaxDiag = 64;     // most diagonals of the DIA form
+constexpr int kDiaSamples = 64;  // rows sampled for the DIA offsets
 constexpr int kShortRow = 32;    // longest row kept in the SELL part of a hybrid
 constexpr int kWarpRow = 1024;   // longest row given one warp; longer: one CTA
 constexpr int kHybBuckets = 61;  // length classes of the hybrid's row sort
@@ -128,6 +138,14 @@ void spmv_scaled(const Ctx& c, const DevCsr<S>& A, const S* x, const double* sca
 // lens[s] = longest row of slice s; then, given the slice offsets, scatter
 // column indices (when sl_col != nullptr) and values.
 void sell_lengths(const Ctx& c, int64_t m, const int64_t* rowptr, const int32_t* perm, int32_t* lens);
+// DIA construction: up to kMaxDiag column offsets (col - row) of kDiaSamples
+// rows spread over the matrix into out[k * (kMaxDiag + 1)] (count first); then
+// dia_val[d * ld + i] = a_{i, i + off[d]} for every entry, *missing set when
+// an entry's offset is not among the ndiag sorted offsets.
+void dia_sample(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* col, int32_t* out);
+template <typename S>
+void dia_fill(const Ctx& c, int64_t n, int64_t ld, const int64_t* rowptr, const int32_t* col, const double* val,
+              int ndiag, const int* off, S* dia_val, int* missing);
 // Hybrid row order: per chunk of kHybChunk rows, counts of every length class
 // (hist[chunk * kHybBuckets + b]); then, from per-chunk starting offsets, the
 // stable counting-sort scatter order[pos] = row.

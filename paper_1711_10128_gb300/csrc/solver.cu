@@ -66,7 +66,53 @@ std::vector<int64_t> slice_offsets(trplk_handle* h, const std::string& tag, int6
 }
 }  // namespace
 
-// SELL-32 copy of a device CSR.  When plain slices would pad the entries by
+// DIA copy when the entries lie on at most kMaxDiag diagonals and the zero
+// padding stays under 30%: candidate offsets from kDiaSamples sample rows, every entry
+// placed by binary search among them (any entry off them: no DIA).
+static bool try_dia(trplk_handle* h, DevCsr<double>& d, const std::string& tag, DevCsr<float>* f32) {
+  const Ctx& c = h->ctx;
+  const int64_t n = d.n;
+  if (n < 64 || d.nnz == 0) return false;
+  auto* smp = static_cast<int32_t*>(h->get(tag + ".dia_smp", kDiaSamples * (kMaxDiag + 1) * sizeof(int32_t)));
+  dia_sample(c, n, d.rowptr, d.col, smp);
+  std::vector<int32_t> hs(kDiaSamples * (kMaxDiag + 1));
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(hs.data(), smp, hs.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  h->sync();
+  std::vector<int> offs;
+  for (int k = 0; k < kDiaSamples; ++k) {
+    const int cnt = hs[k * (kMaxDiag + 1)];
+    if (cnt < 0) return false;
+    for (int e = 0; e < cnt; ++e) offs.push_back(hs[k * (kMaxDiag + 1) + 1 + e]);
+  }
+  std::sort(offs.begin(), offs.end());
+  offs.erase(std::unique(offs.begin(), offs.end()), offs.end());
+  const int nd = (int)offs.size();
+  if (nd == 0 || nd > kMaxDiag) return false;
+  if ((double)nd * (double)n > 1.3 * (double)d.nnz) return false;
+  const int64_t ld = round_up(n, 256);
+  auto* miss = static_cast<int*>(h->get(tag + ".dia_miss", sizeof(int), true));
+  auto* dv = static_cast<double*>(h->get(tag + ".dia_val", (size_t)nd * ld * sizeof(double), true));
+  dia_fill<double>(c, n, ld, d.rowptr, d.col, d.val, nd, offs.data(), dv, miss);
+  int hm = 0;
+  TRPLK_CUDA_TRY(cudaMemcpyAsync(&hm, miss, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  h->sync();
+  if (hm) return false;
+  d.dia_val = dv;
+  d.dia_ld = ld;
+  d.ndiag = nd;
+  for (int k = 0; k < nd; ++k) d.dia_off[k] = offs[k];
+  if (f32) {
+    auto* dvf = static_cast<float*>(h->get(tag + ".dia_valf", (size_t)nd * ld * sizeof(float)));
+    convert<float, double>(c, (int64_t)nd * ld, dv, dvf);
+    f32->dia_val = dvf;
+    f32->dia_ld = ld;
+    f32->ndiag = nd;
+    for (int k = 0; k < nd; ++k) f32->dia_off[k] = offs[k];
+  }
+  return true;
+}
+
+// SELL-32 copy of a device CSR (or the DIA copy, see try_dia).  When plain slices would pad the entries by
 // more than 25% (rows of very unequal length), the hybrid form is built
 // instead: rows ordered by length class (a stable counting sort: per-chunk
 // class counts on the device, their prefix sums here), the longest rows
@@ -74,6 +120,7 @@ std::vector<int64_t> slice_offsets(trplk_handle* h, const std::string& tag, int6
 void attach_sell(trplk_handle* h, DevCsr<double>& d, const std::string& tag, DevCsr<float>* f32) {
   const Ctx& c = h->ctx;
   const int64_t n = d.n;
+  if (try_dia(h, d, tag, f32)) return;
   std::vector<int64_t> ptr = slice_offsets(h, tag, n, d.rowptr, nullptr);
   const int64_t nslices = (n + 31) / 32;
   if ((double)ptr[nslices] <= 1.25 * (double)d.nnz + 32.0 * nslices) {

@@ -1,7 +1,9 @@
 // Sparse matrix-vector products and small elementwise kernels.
 //
-// SpMV (eq. (UpdateT), z = A g).  Operators whose rows have similar lengths
-// (stencils, FEM) are converted to SELL-32 at set-up and multiplied by
+// SpMV (eq. (UpdateT), z = A g).  Operators whose entries lie on a few
+// diagonals (stencils, structured FEM) are converted to DIA at set-up
+// (dia_spmv_kernel: no column indices).  Other operators whose rows have
+// similar lengths are converted to SELL-32 and multiplied by
 // sell_spmv_kernel below.  Operators with very unequal rows (power-law graphs)
 // get the hybrid form of the same kernel: rows sorted by length class, short
 // rows in SELL-32 slices, long rows one warp each, the longest one CTA each.
@@ -216,10 +218,56 @@ __global__ void __launch_bounds__(256) sell_spmv_kernel(
   if (pos < m) spmv_finish<S, SCALED>(HYB ? (int64_t)perm[pos] : pos, sum, x, y, scale, g, bx, bg);
 }
 
+struct DiaOff {
+  int off[kMaxDiag];
+};
+
+// DIA matvec: thread per row, one coalesced load of each diagonal's value and
+// of the shifted x window (x stays in L2); no index traffic.
+template <typename S, bool SCALED>
+__global__ void __launch_bounds__(256) dia_spmv_kernel(int64_t n, int64_t ld, int ndiag, const DiaOff off,
+                                                       const S* __restrict__ dval, const S* __restrict__ x,
+                                                       S* __restrict__ y, const double* __restrict__ scale,
+                                                       S* __restrict__ g, const S* __restrict__ bx,
+                                                       S* __restrict__ bg) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  S s0 = 0, s1 = 0;
+  int d = 0;
+  for (; d + 1 < ndiag; d += 2) {
+    const int64_t j0 = i + off.off[d], j1 = i + off.off[d + 1];
+    const S a0 = __ldg(dval + (int64_t)d * ld + i), a1 = __ldg(dval + (int64_t)(d + 1) * ld + i);
+    if ((uint64_t)j0 < (uint64_t)n) s0 = fmaS(a0, __ldg(x + j0), s0);
+    if ((uint64_t)j1 < (uint64_t)n) s1 = fmaS(a1, __ldg(x + j1), s1);
+  }
+  if (d < ndiag) {
+    const int64_t j0 = i + off.off[d];
+    if ((uint64_t)j0 < (uint64_t)n) s0 = fmaS(__ldg(dval + (int64_t)d * ld + i), __ldg(x + j0), s0);
+  }
+  spmv_finish<S, SCALED>(i, s0 + s1, x, y, scale, g, bx, bg);
+}
+
 template <typename S>
 void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const double* scale, S* g,
                  const S* bx, S* bg, bool scaled) {
   if (A.n == 0) return;
+  if (A.dia_val) {
+    DiaOff off;
+    for (int d = 0; d < kMaxDiag; ++d) off.off[d] = d < A.ndiag ? A.dia_off[d] : 0;
+    // algorithmic bytes: the diagonals' values, x once, y (and the scaled copies) once
+    double bytes = (double)A.ndiag * A.n * sizeof(S) + 2.0 * A.n * sizeof(S);
+    if (scaled) bytes += (double)A.n * sizeof(S) * (bx ? 3 : 1);
+    ProfScope ps(c, prof_kind<S>(scaled ? PK_SPMV_SCALED : PK_SPMV), bytes);
+    const unsigned gb = (unsigned)((A.n + 255) / 256);
+    if (scaled)
+      dia_spmv_kernel<S, true><<<gb, 256, 0, c.stream>>>(A.n, A.dia_ld, A.ndiag, off, A.dia_val, x, y, scale, g, bx,
+                                                         bg);
+    else
+      dia_spmv_kernel<S, false><<<gb, 256, 0, c.stream>>>(A.n, A.dia_ld, A.ndiag, off, A.dia_val, x, y, nullptr,
+                                                          nullptr, nullptr, nullptr);
+    check_launch("dia_spmv_kernel");
+    return;
+  }
   if (A.sl_ptr) {
     const bool hyb = A.sl_perm || A.long_rows;
     const int64_t m = hyb ? A.sl_rows : A.n;
@@ -370,6 +418,45 @@ __global__ void sell_fill_kernel(int64_t m, const int64_t* __restrict__ rowptr, 
   }
 }
 
+// kDiaSamples rows along a Weyl sequence (fractional parts of k times the
+// golden ratio, so no sample lines up with the grid boundaries of a
+// power-of-two stencil); their first kMaxDiag column offsets
+__global__ void dia_sample_kernel(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                  int32_t* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k >= kDiaSamples) return;
+  const uint64_t frac = (uint64_t)(uint32_t)((uint64_t)(k + 1) * 2654435769ull);   // 2^32 frac(k phi)
+  const int64_t i = (int64_t)((frac * (uint64_t)n) >> 32);
+  int32_t* o = out + k * (kMaxDiag + 1);
+  const int64_t rs = rowptr[i], re = rowptr[i + 1];
+  const int cnt = (int)(re - rs < kMaxDiag ? re - rs : kMaxDiag);
+  o[0] = re - rs > kMaxDiag ? -1 : cnt;   // -1: too many entries for DIA
+  for (int e = 0; e < cnt; ++e) o[1 + e] = (int32_t)((int64_t)col[rs + e] - i);
+}
+
+struct DiaOffSorted {
+  int off[kMaxDiag];
+};
+
+template <typename S>
+__global__ void dia_fill_kernel(int64_t n, int64_t ld, const int64_t* __restrict__ rowptr,
+                                const int32_t* __restrict__ col, const double* __restrict__ val, int ndiag,
+                                const DiaOffSorted off, S* __restrict__ dval, int* __restrict__ missing) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int64_t o = (int64_t)col[e] - i;
+      int lo = 0, hi = ndiag - 1, d = -1;
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        if (off.off[mid] == o) { d = mid; break; }
+        if (off.off[mid] < o) lo = mid + 1; else hi = mid - 1;
+      }
+      if (d < 0) { atomicOr(missing, 1); continue; }
+      dval[(int64_t)d * ld + i] = (S)val[e];
+    }
+  }
+}
+
 // length class of a row: the longest first.  [0, 22): more than kWarpRow
 // entries, by descending floor(log2 len); [22, 28): kShortRow+1 .. kWarpRow,
 // likewise; [28, 61): 0 .. kShortRow entries, by descending length.
@@ -495,6 +582,26 @@ void sell_fill(const Ctx& c, int64_t m, const int64_t* rowptr, const int32_t* co
                                                                                     sl_ptr, sl_col, sl_val);
   check_launch("sell_fill");
 }
+
+void dia_sample(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* col, int32_t* out) {
+  ProfScope ps(c, PK_OTHER, 0.0);
+  dia_sample_kernel<<<1, kDiaSamples, 0, c.stream>>>(n, rowptr, col, out);
+  check_launch("dia_sample");
+}
+
+template <typename S>
+void dia_fill(const Ctx& c, int64_t n, int64_t ld, const int64_t* rowptr, const int32_t* col, const double* val,
+              int ndiag, const int* off, S* dia_val, int* missing) {
+  DiaOffSorted o;
+  for (int d = 0; d < kMaxDiag; ++d) o.off[d] = d < ndiag ? off[d] : 0;
+  ProfScope ps(c, PK_OTHER, 0.0);
+  dia_fill_kernel<S><<<grid_for(c, n), 256, 0, c.stream>>>(n, ld, rowptr, col, val, ndiag, o, dia_val, missing);
+  check_launch("dia_fill");
+}
+template void dia_fill<double>(const Ctx&, int64_t, int64_t, const int64_t*, const int32_t*, const double*, int,
+                               const int*, double*, int*);
+template void dia_fill<float>(const Ctx&, int64_t, int64_t, const int64_t*, const int32_t*, const double*, int,
+                              const int*, float*, int*);
 
 void hyb_hist(const Ctx& c, int64_t n, const int64_t* rowptr, int32_t* hist) {
   const int64_t chunks = (n + kHybChunk - 1) / kHybChunk;

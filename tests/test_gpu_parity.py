@@ -139,6 +139,32 @@ def test_spmv_hybrid_rows_match_oracle(lib, h, prec):
     assert empty.size > 0 and np.all(y.cpu().numpy()[empty] == 0)
 
 
+def test_spmv_storage_form_follows_the_structure(lib, h):
+    """Stencil and FEM operators take the diagonal (DIA) form -- the profiler's
+    algorithmic bytes of the matvec are ndiag n 8 + 2 n 8, no index traffic --
+    and a power-law graph does not; the results match the oracle either way."""
+    def matvec_bytes(A):
+        x = np.random.default_rng(3).standard_normal(A.n)
+        y = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        lib.trplk_profile(h, 1)
+        lib.trplk_spmv(h, dev_csr(lib, A), dev(x), y)
+        n_l, ms, by = lib.trplk_profile_read(h, 12)   # spmv on FP64 data
+        lib.trplk_profile(h, 0)
+        ref = O.spmv(A.to_scipy(), x)
+        assert np.allclose(y.cpu().numpy(), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+        return n_l, by
+    for A, nd in ((W.laplacian_2d(37), 5), (W.diffusion_3d(13, W.lognormal_field(13, 1.0, 3)), 7),
+                  (W.fem_q1_pencil(12, np.random.default_rng(4).uniform(1, 10, (12, 12, 12)))[0], 27)):
+        n_l, by = matvec_bytes(A)
+        assert n_l == 1 and by == nd * A.n * 8 + 2 * A.n * 8
+    # too much zero padding (35%: boundary rows of a 7^3 Q1 operator) or too
+    # many diagonals (a power-law graph): another form, never the DIA bytes
+    for A in (W.fem_q1_pencil(7, np.random.default_rng(4).uniform(1, 10, (7, 7, 7)))[0],
+              W.chung_lu_laplacian(3000, 8.0, 2.1, 3)):
+        n_l, by = matvec_bytes(A)
+        assert n_l == 1 and by > A.nnz * 12
+
+
 def test_spmv_full_size_sampled_rows(lib, h):
     """128^3 lognormal diffusion (n = 2,097,152): sampled rows against the
     oracle's row dot products."""
