@@ -193,9 +193,11 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_for(kernel_family):
-    """DRAM traffic per launch of a kernel family from the committed ncu
-    summary, if the kernel sources are unchanged since it was taken."""
+def traffic_for(kernel_family, algorithmic_bytes_per_launch):
+    """DRAM traffic per launch of a kernel family: the DRAM bytes per
+    algorithmic byte measured by ncu on this workload (profiles/traffic.json)
+    times the launch's algorithmic bytes -- None if the kernel sources changed
+    since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -208,7 +210,7 @@ def traffic_for(kernel_family):
         h.update(open(os.path.join(ROOT, f), "rb").read())
     if h.hexdigest() != ent.get("sha256"):
         return None
-    return ent.get("bytes_per_launch_full_size")
+    return ent["dram_per_algorithmic_byte"] * algorithmic_bytes_per_launch
 
 
 # ---------------------------------------------------------------- CPU oracle sample
@@ -405,7 +407,7 @@ def run_ours(args, world, rank, local, pg):
         achieved = by / (tms / 1e3) / 1e9
         out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                            "frac": achieved / hbm_peak, "peak_source": peak_src,
-                           "traffic": traffic_for(dom) if P["key"] == "diffusion128" else None,
+                           "traffic": traffic_for(dom, by / nl) if P["key"] == "diffusion128" else None,
                            "launches": nl, "avg_launch_us": tms * 1e3 / nl,
                            "algorithmic_bytes_per_launch": by / nl}
     tot = sum(v[1] for v in prof.values()) or 1.0
