@@ -624,9 +624,11 @@ struct Solver {
           hist_t = t;
         }
         hist.push_back(rel);
-        // only below 1e-6, where FP32 rounding can hold a residual up
-        if (!cv[t] && rel < 1e-6 && (int)hist.size() > stall_window &&
-            rel > 0.5 * hist[hist.size() - 1 - stall_window]) {
+        // not halved over stall_window cycles below 1e-6 (where FP32 rounding
+        // can hold a residual up), or over 4 stall_window cycles at any level
+        // (a guard: the FP64 continuation then takes over)
+        auto flat = [&](int win) { return (int)hist.size() > win && rel > 0.5 * hist[hist.size() - 1 - win]; };
+        if (!cv[t] && ((rel < 1e-6 && flat(stall_window)) || flat(4 * stall_window))) {
           stalled = true;
           out.theta = th;
           out.cur = cur;
@@ -821,7 +823,8 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
     } else {
       // FP32 phase: to mixed_tol, by default max(tol, 3e-8) -- about half the
       // FP32 unit roundoff, the level at which Ritz vectors stored in FP32 stop
-      // improving; a target stuck below 1e-6 for 30 cycles also ends the phase
+      // improving; a target stuck below 1e-6 for 30 cycles, or not halving its
+      // residual in 120 cycles at any level, also ends the phase
       const double tol32 = P->mixed_tol > 0.0 ? P->mixed_tol : std::max(P->tol, 3e-8);
       Solver<float> S32(h, "f32", n, P->p, P->q, P->k, P->l, std::max(tol32, P->tol), P->max_cycles, Aop, Bop, hasB,
                         dinv32, pmode);
