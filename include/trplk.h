@@ -103,8 +103,11 @@ typedef struct {
  *             runs the MLP with BF16 weights/activations (FP32 accumulation)
  *  mixed_tol  FP32-phase tolerance of the mixed path (0 = max(tol, 3e-8));
  *             the FP32 phase also stops when the target's relative residual,
- *             once below 1e-6, has not halved over 30 cycles; FP64 cycles
- *             then finish to tol                                         */
+ *             once below 1e-6, has not halved over 30 cycles (at any level:
+ *             120 cycles); FP64 cycles from its Ritz vectors then finish to
+ *             tol -- each starting from the preconditioned residuals of all
+ *             pairs within 100x of tol, basis min(q, k + p + 4 + l) -- and
+ *             info.refine_cycles counts them                             */
 typedef struct {
   int p, q, k, l;
   double tol;
@@ -174,7 +177,11 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
  * ---------------------------------------------------------------------- */
 
 /* y = A x (the matvec of eq. (UpdateT)).  A on device, val of `A->dtype`;
- * x, y of that dtype, length n.  y must not alias x. */
+ * x, y of that dtype, length n.  y must not alias x.  The storage form is
+ * chosen from A's structure on each call, as in trplk_solve: diagonals (DIA,
+ * at most 64 of them, <= 30% zero padding), SELL-32 slices (<= 25% padding),
+ * or the hybrid of SELL slices and warp/CTA-per-row for long rows.  A's CSR
+ * structure is not validated here (trplk_solve validates it). */
 trplk_status trplk_spmv(trplk_handle* h, const trplk_csr* A, const void* x, void* y);
 
 /* The fused T-column / preconditioner / first-projection pass of one inner
