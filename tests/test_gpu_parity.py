@@ -727,3 +727,38 @@ def test_full_size_chunglu22_mixed_at_tol_1e12_matches_oracle(lib, h):
     rel = np.abs(ev - refev) / np.abs(refev)
     print("mixed Chung-Lu at tol 1e-12: eigenvalue error vs oracle (relative): max", rel.max())
     assert np.all(rel <= 1e-10), rel
+
+
+def _lap3d_eigs(N, count):
+    s = 4 * np.sin(np.arange(1, N + 1) * np.pi / (2 * (N + 1))) ** 2
+    return np.sort((s[:, None, None] + s[None, :, None] + s[None, None, :]).ravel())[:count]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_closed_forms(lib, h, precision):
+    """The full-size 128^3 diffusion operator with all coefficients 1 (the 3D
+    Laplacian, n = 2,097,152; the wanted 10 end with a complete triple) at tol
+    1e-10: each computed eigenvalue lies within the Kato-Temple bound
+    ||r||^2 / gap of its closed form (r the recomputed residual of the returned
+    unit vector, gap the distance to the nearest distinct eigenvalue) plus the
+    FP64 rounding floor of a Ritz value, 64 u ||A||_1 (u = 2^-52), and within
+    1e-10 relative."""
+    prec = lib.PRECISION_FP64 if precision == "fp64" else lib.PRECISION_MIXED
+    A = W.diffusion_3d(128)
+    lam_all = _lap3d_eigs(128, 11)
+    p = 10
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), None, p=p, q=40, k=15, l=1, tol=1e-10, seed=0,
+                                     precision=prec)
+    assert rc == lib.OK
+    lam = lam_all[:p]
+    uniq = np.unique(np.round(lam_all, 12))
+    gap = np.array([np.min(np.abs(uniq[np.abs(uniq - x) > 1e-9 * x] - x)) for x in lam])
+    As = A.to_scipy()
+    R = As @ X - X * ev
+    r2 = np.sum(R * R, axis=0) / np.sum(X * X, axis=0)
+    err = np.abs(ev - lam)
+    floor = 64 * 2.0 ** -52 * O.norm1(As)
+    print(precision, "closed-form error (relative): max", (err / lam).max(), "absolute max", err.max(),
+          "rounding floor", floor)
+    assert np.all(err <= r2 / gap + floor)
+    assert np.all(err <= 1e-10 * lam)

@@ -318,3 +318,18 @@ def test_closed_form_values_c1():
     assert abs(lam[1] - lam[2]) < 1e-17 and abs(lam[3] - 7.737611465622606e-3) < 1e-17
     brute = np.linalg.eigvalsh(W.laplacian_2d(12).to_scipy().toarray())[:6]
     assert np.allclose(brute, lap2d_eigs(12, 6), rtol=1e-13)
+
+
+def test_closed_form_values_full_size_c2_c3():
+    """The 3D Laplacian (128^3, all coefficients 1) and the constant-E Q1 pencil
+    (96^3 elements) formulas at full size, against the values computed
+    independently for these configurations: smallest and last-wanted eigenvalue
+    and the multiplicities that end each wanted set."""
+    lam = lap3d_eigs(128, 12)
+    assert abs(lam[0] - 1.779180929164e-3) < 1e-15
+    assert abs(lam[9] - 6.521553292339e-3) < 1e-15
+    assert abs(lam[7] - lam[9]) < 1e-17 and lam[10] > lam[9] + 1e-4   # (1,1,3) triple closes the 10
+    mu = fem_eigs(96, 21)
+    assert abs(mu[0] - 7.4023684517) < 1e-9
+    assert abs(mu[19] - 1.0614157990e2) < 1e-7
+    assert abs(mu[17] - mu[19]) < 1e-9 and mu[20] > mu[19] + 1.0      # (2,2,3) triple closes the 20
