@@ -3,7 +3,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "trplk.h"
@@ -54,6 +56,25 @@ struct Error {
   std::string msg;
   Error(trplk_status c, std::string m) : code(c), msg(std::move(m)) {}
 };
+
+// Opt kernel `Kernel` into `bytes` of dynamic shared memory on `device`, once
+// per (kernel, device): the attribute is kept per device, and a process may
+// hold handles on several GPUs.  Lock-free after the first call.
+template <auto Kernel>
+void smem_optin(int bytes, int device) {
+  static std::atomic<unsigned long long> done{0};
+  static std::mutex mu;
+  const unsigned long long bit = 1ull << (device & 63);
+  if (done.load(std::memory_order_acquire) & bit) return;
+  std::lock_guard<std::mutex> g(mu);
+  if (done.load(std::memory_order_relaxed) & bit) return;
+  const cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(TRPLK_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+  }
+  done.fetch_or(bit, std::memory_order_release);
+}
 
 inline void check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();

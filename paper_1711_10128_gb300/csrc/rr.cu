@@ -310,11 +310,7 @@ void rayleigh_ritz(const Ctx& c, int w, const double* T, int ldT, double* theta,
     const size_t wp = (size_t)(ww + (ww & 1));
     return wp * (wp + 1) * (4 * sizeof(double) + 2 * sizeof(float));
   };
-  static bool cfg = false;
-  if (!cfg) {
-    TRPLK_CUDA_TRY(cudaFuncSetAttribute(rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes(kMaxQ)));
-    cfg = true;
-  }
+  smem_optin<rr_kernel>((int)bytes(kMaxQ), c.device);
   ProfScope ps(c, PK_RR, 0.0);
   rr_kernel<<<1, kThreads, bytes(w), c.stream>>>(w, T, ldT, theta, Y, c.status);
   check_launch("rr_kernel");

@@ -305,12 +305,10 @@ void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const doubl
   if (scaled) bytes += (double)A.n * sizeof(S) * (bx ? 3 : 1);
   ProfScope ps(c, prof_kind<S>(scaled ? PK_SPMV_SCALED : PK_SPMV), bytes);
   if (scaled) {
-    static bool cfg = false;
-    if (!cfg) { TRPLK_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); cfg = true; }
+    smem_optin<spmv_kernel<S, true>>((int)smem, c.device);
     spmv_kernel<S, true><<<(unsigned)blocks, kRows, smem, c.stream>>>(A.n, A.rowptr, A.col, A.val, x, y, scale, g, bx, bg);
   } else {
-    static bool cfg = false;
-    if (!cfg) { TRPLK_CUDA_TRY(cudaFuncSetAttribute(spmv_kernel<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); cfg = true; }
+    smem_optin<spmv_kernel<S, false>>((int)smem, c.device);
     spmv_kernel<S, false><<<(unsigned)blocks, kRows, smem, c.stream>>>(A.n, A.rowptr, A.col, A.val, x, y, nullptr, nullptr, nullptr, nullptr);
   }
   check_launch("spmv_kernel");

@@ -1,5 +1,6 @@
 // Launchers of the tall-skinny streaming kernels (see tallskinny.cuh).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "launch.h"
@@ -12,20 +13,23 @@ namespace {
 constexpr size_t kSmemMax = 232448 - 1024;   // opt-in shared memory per CTA less static use
 constexpr size_t kSmemPerSM = 233472;        // shared memory per SM
 
-// CTAs of one instantiation that fit on an SM by registers and threads.
+// CTAs of one instantiation that fit on an SM by registers and threads (the
+// same on every device of this architecture); opts the kernel into the full
+// shared memory on `device`.
 template <typename S, int KIND, int MAXW>
-int regs_limit() {
-  static int lim = 0;
-  if (!lim) {
+int regs_limit(int device) {
+  static std::atomic<int> lim{0};
+  int l = lim.load(std::memory_order_relaxed);
+  if (!l) {
     cudaFuncAttributes fa;
     TRPLK_CUDA_TRY(cudaFuncGetAttributes(&fa, ts_kernel<S, KIND, MAXW>));
     const int threads = Tile<S>::TR + 32;
     const int regs = std::max(fa.numRegs, 1) * threads;
-    lim = std::max(1, std::min(65536 / regs, 2048 / threads));
-    TRPLK_CUDA_TRY(cudaFuncSetAttribute(ts_kernel<S, KIND, MAXW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kSmemMax));
+    l = std::max(1, std::min(65536 / regs, 2048 / threads));
+    lim.store(l, std::memory_order_relaxed);
   }
-  return lim;
+  smem_optin<ts_kernel<S, KIND, MAXW>>((int)kSmemMax, device);
+  return l;
 }
 
 template <typename S, int KIND, int MAXW>
@@ -34,7 +38,7 @@ void launch_kind(const Ctx& c, TSArgs<S>& a, size_t fixed, size_t stage, double 
   // producer/consumer group per SM hides more latency than deeper pipelines
   // of one group, e.g. 56.7 us against 87.5 us for the FP32 update+norm pass
   // at n = 2^21, w = 32), then as many stages as fit, up to 8.
-  const int lim = regs_limit<S, KIND, MAXW>();
+  const int lim = regs_limit<S, KIND, MAXW>(c.device);
   int per_sm = 1, stages = 0;
   for (int cand = lim; cand >= 1; --cand) {
     const size_t per_cta = std::min<size_t>(kSmemMax, kSmemPerSM / cand - 1024);
