@@ -444,7 +444,9 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(
       }
     }
     __syncthreads();
-    // weight-gradient entries owned by this thread: e = tid + 128 q
+    // weight-gradient entries owned by this thread: e = tid + 128 q (the entry
+    // loop is unrolled so acc stays in registers; the row loops are not, which
+    // keeps the kernel small -- the order of every sum is the same either way)
 #pragma unroll
     for (int q = 0; q < kEntPerThread; ++q) {
       const int e = tid + 128 * q;
@@ -452,21 +454,27 @@ __global__ void __launch_bounds__(128) mlp_backward_kernel(
       float s = 0.f;
       if (e < OFF_B1) {                 // W1[k][c]: dh1_k f_c
         const int k = e >> 3, c = e & 7;
+#pragma unroll 1
         for (int r = 0; r < kBR; ++r) s = fmaf(rows[r * kRowF + 208 + k], rows[r * kRowF + c], s);
       } else if (e < OFF_W2) {          // b1[k]
         const int k = e - OFF_B1;
+#pragma unroll 1
         for (int r = 0; r < kBR; ++r) s += rows[r * kRowF + 208 + k];
       } else if (e < OFF_B2) {          // W2[k][j]: dh2_k h1_j
         const int k = (e - OFF_W2) >> 6, j = (e - OFF_W2) & 63;
+#pragma unroll 1
         for (int r = 0; r < kBR; ++r) s = fmaf(rows[r * kRowF + 144 + k], rows[r * kRowF + 8 + j], s);
       } else if (e < OFF_W3) {          // b2[k]
         const int k = e - OFF_B2;
+#pragma unroll 1
         for (int r = 0; r < kBR; ++r) s += rows[r * kRowF + 144 + k];
       } else if (e < OFF_B3) {          // W3[q][k]: dO_q h2_k
         const int qq = (e - OFF_W3) >> 6, k = (e - OFF_W3) & 63;
+#pragma unroll 1
         for (int r = 0; r < kBR; ++r) s = fmaf(rows[r * kRowF + 136 + qq], rows[r * kRowF + 72 + k], s);
       } else {                          // b3[q]
         const int qq = e - OFF_B3;
+#pragma unroll 1
         for (int r = 0; r < kBR; ++r) s += rows[r * kRowF + 136 + qq];
       }
       acc[q] += s;
