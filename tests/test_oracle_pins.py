@@ -333,3 +333,20 @@ def test_closed_form_values_full_size_c2_c3():
     assert abs(mu[0] - 7.4023684517) < 1e-9
     assert abs(mu[19] - 1.0614157990e2) < 1e-7
     assert abs(mu[17] - mu[19]) < 1e-9 and mu[20] > mu[19] + 1.0      # (2,2,3) triple closes the 20
+
+
+def test_breakdown_on_an_invariant_krylov_space_still_gives_exact_eigenpairs():
+    """Reading R5: with three distinct eigenvalues (multiplicity 4 each) and
+    M = I the Krylov space of one start vector is invariant after at most
+    three steps; the inner loop ends early and the Rayleigh-Ritz step still
+    yields the smallest eigenvalue exactly."""
+    rng = np.random.default_rng(5)
+    lam = np.repeat([1.0, 2.5, 4.0], 4)
+    Q = np.linalg.qr(rng.standard_normal((12, 12)))[0]
+    A = sp.csr_matrix((Q * lam) @ Q.T)
+    r = O.solve(A, None, 1, 10, 1, 0, 1e-12, W.start_block(12, 1, 3), None)
+    assert r["status"] in (O.OK, O.BREAKDOWN)
+    assert r["cycles"] == 1 and r["mv_A"] < 1 + (10 - 1)   # the cycle stopped before its 9 inner steps
+    assert abs(r["evals"][0] - 1.0) <= 1e-12
+    x = r["evecs"][:, 0]
+    assert np.linalg.norm(A @ x - x) <= 1e-10
