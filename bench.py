@@ -1,28 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of the TRPL+K hot path on one GB300 (or N independent replicas).
 
-Workload: the 3D 7-point variable-coefficient diffusion operator on 128^3
-cells (n = 2,097,152, nnz = 14,581,760, FP64 CSR), coefficients
-lognormal(0, 1) per cell (seed 1); the 10 smallest eigenpairs, Jacobi
-preconditioner, q = 40, p_hat = 15, +K = 1, tol 1e-8 (relative to ||A||_1),
-start block SplitMix64 seed 0.  One step = one whole solve (start block,
-Rayleigh-Ritz, every TRPL+K cycle, FP64 refinement, final FP64 residual
-check).
+Workload (the default): L + 1e-3 I of a Chung-Lu random graph on 2^22
+vertices (mean degree 16, degree exponent 2.1, seed 3), restricted to its
+largest component (n = 4,117,504, nnz = 71,231,354, rows of 2..8220
+entries); the 16 smallest eigenpairs, Jacobi preconditioner, q = 40,
+p_hat = 20, +K = 1, tol 1e-8 (relative to ||A||_1), start block SplitMix64
+seed 0.  One step = one whole solve (start block, Rayleigh-Ritz, every TRPL+K
+cycle, FP64 refinement, final FP64 residual check).
 
 Reported: seconds per solve of the mixed path (FP32 basis and SpMV,
 FP64-class coefficients, FP64 refinement) with inputs resident in HBM
-(`value`), the plain FP64 path on the same matrix (`fp64_seconds`), the same
-mixed solve end to end from pinned host memory (`e2e`), the roofline of the
-dominant kernel family measured with CUDA events inside the timed region,
-the SpMV bandwidth, and the CPU oracle on a bounded sample (`cpu_baseline`).
+(`value`), the plain FP64 path on the same matrix (`fp64_seconds`), each
+result's largest eigenvalue error against the oracle's stored run of the same
+workload (`eig_err_vs_oracle`), the same mixed solve end to end from pinned
+host memory (`e2e`), the roofline of the dominant kernel family measured with
+CUDA events inside the timed region, the SpMV bandwidth, the CPU oracle on a
+bounded sample (`cpu_baseline`), and the learned preconditioner on the
+anisotropic 128^3 family (`learned`): an MLP trained on 200 seeded 32^3
+operators (seeds 1000-1199), then learned FSAI, Jacobi and classical FSAI,
+each mixed and FP64, on 20 held-out 128^3 operators (seeds 2000-2019).
 
-`--workload` selects another operator class (the default is the one above):
-q1pencil96 (trilinear Q1 stiffness/mass pencil on 96^3 elements, 20
-smallest, q = 50, p_hat = 25), chunglu22 (L + 1e-3 I of a 2^22-vertex
-Chung-Lu graph's largest component, 16 smallest, q = 40, p_hat = 20),
-aniso128 (anisotropic 128^3 diffusion, 20 smallest, q = 50, p_hat = 25, with
-the learned FSAI preconditioner trained first on twelve 32^3 operators of the
-family, compared against Jacobi and classical FSAI in both precisions).
+`--workload` selects another operator class for the headline: diffusion128
+(3D 7-point lognormal(0, 1) diffusion on 128^3, 10 smallest, q = 40,
+p_hat = 15), q1pencil96 (trilinear Q1 stiffness/mass pencil on 96^3
+elements, 20 smallest, q = 50, p_hat = 25), aniso128 (one held-out
+anisotropic 128^3 operator with the learned FSAI, compared against Jacobi and
+classical FSAI in both precisions).  `--learned-ops 0` skips the learned block.
 
 `--impl reference` times the CPU oracle (FP64 numpy/scipy) instead.
 Multi-GPU: one process per GPU (torchrun); the path does not shard, so each
@@ -56,10 +60,13 @@ WORKLOADS = {
     # anisotropic 7-point diffusion on 128^3 (held-out operator, seed 2000): learned FSAI trained on
     # twelve 32^3 operators of the same family (seeds 1000-1011), against Jacobi and classical FSAI
     "aniso128": dict(name="anisotropic_diffusion_128_learned_fsai", N=128, op_seed=2000, train_N=32,
-                     train_seeds=list(range(1000, 1012)), p=20, q=50, k=25, l=1, tol=1e-8, seed=0,
+                     train_seeds=list(range(1000, 1200)), p=20, q=50, k=25, l=1, tol=1e-8, seed=0,
                      precond="fsai_learned"),
 }
-WORKLOAD = dict(WORKLOADS["diffusion128"], key="diffusion128")
+# held-out operators of the learned block (anisotropic family, 128^3)
+HELD_OUT_SEEDS = list(range(2000, 2020))
+DEFAULT_WORKLOAD = "chunglu22"
+WORKLOAD = dict(WORKLOADS[DEFAULT_WORKLOAD], key=DEFAULT_WORKLOAD)
 METRIC = "s to p eigpairs @resid 1e-8, learned/FP32 vs plain FP64; SpMV HBM GB/s"
 
 
@@ -72,9 +79,12 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solves")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="diffusion128", choices=sorted(WORKLOADS),
-                    help="diffusion128 is the headline; the others measure the remaining operator classes")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
+                    help="chunglu22 is the headline; the others measure the remaining operator classes")
+    ap.add_argument("--learned-ops", type=int, default=len(HELD_OUT_SEEDS),
+                    help="held-out anisotropic 128^3 operators of the learned block (0 skips it)")
     args = ap.parse_args()
+    args.learned_ops = max(0, min(args.learned_ops, len(HELD_OUT_SEEDS)))
     global WORKLOAD
     WORKLOAD = dict(WORKLOADS[args.workload], key=args.workload)
     return args
@@ -193,16 +203,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_for(kernel_family, algorithmic_bytes_per_launch):
-    """DRAM traffic per launch of a kernel family: the DRAM bytes per
-    algorithmic byte measured by ncu on this workload (profiles/traffic.json)
-    times the launch's algorithmic bytes -- None if the kernel sources changed
-    since the counters were taken."""
+def traffic_for(workload_key, kernel_family, algorithmic_bytes_per_launch):
+    """DRAM traffic per launch of a kernel family on a workload: the DRAM bytes
+    per algorithmic byte that ncu measured for it (profiles/traffic.json, key
+    "<workload>/<family>") times the launch's algorithmic bytes -- None if no
+    capture exists or a kernel source changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    ent = d.get(kernel_family)
+    ent = d.get(f"{workload_key}/{kernel_family}")
     if not ent:
         return None
     h = hashlib.sha256()
@@ -211,6 +221,27 @@ def traffic_for(kernel_family, algorithmic_bytes_per_launch):
     if h.hexdigest() != ent.get("sha256"):
         return None
     return ent["dram_per_algorithmic_byte"] * algorithmic_bytes_per_launch
+
+
+def stored_oracle_run(key):
+    """The oracle's stored converged run of a workload (oracle/reference_runs.json,
+    written by oracle/reference_runs.py), or None.  Only the stored numbers are
+    read: nothing of the oracle runs here."""
+    path = os.path.join(ROOT, "oracle", "reference_runs.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(key)
+    return d if d and d.get("status") == "ok" else None
+
+
+def eig_error(ev, ref):
+    """Largest relative eigenvalue error against a stored oracle run."""
+    import numpy as np
+    if ref is None:
+        return None
+    r = np.asarray(ref["evals"], dtype=np.float64)
+    e = np.asarray(ev, dtype=np.float64)[: r.size]
+    return float(np.max(np.abs(e - r) / np.abs(r)))
 
 
 # ---------------------------------------------------------------- CPU oracle sample
@@ -275,11 +306,12 @@ def run_reference(args, world, rank, pg):
 
 # ---------------------------------------------------------------- our path
 def train_learned_fsai(lib, h, dev):
-    """Train the learned-FSAI MLP on the training operators of the workload;
-    returns (weights, seconds, first and last mean loss)."""
+    """Train the learned-FSAI MLP on the anisotropic family's training
+    operators (200 seeded 32^3 operators, seeds 1000-1199); returns (weights,
+    seconds, first and last mean loss, number of operators, grid)."""
     import torch
     from paper_1711_10128_gb300 import workloads as W
-    w = WORKLOAD
+    w = WORKLOADS["aniso128"]
     N = w["train_N"]
     ops = []
     for s in w["train_seeds"]:
@@ -287,6 +319,7 @@ def train_learned_fsai(lib, h, dev):
         ops.append(lib.make_csr(torch.from_numpy(T.rowptr).to(dev), torch.from_numpy(T.col).to(dev),
                                 torch.from_numpy(T.val).to(dev)))
     weights = lib.trplk_fsai_mlp_init(0)
+    # 20 Adam steps per operator, the operators visited in turn
     tp = lib.trplk_train_params(iters=20 * len(ops), lr=2e-3, vectors=8, harvest_cycles=6, q=24, k=10, l=1, seed=5,
                                 bf16=1, gamma=0.1)
     torch.cuda.synchronize(dev)
@@ -295,10 +328,89 @@ def train_learned_fsai(lib, h, dev):
     torch.cuda.synchronize(dev)
     secs = time.perf_counter() - t0
     m = len(ops)
-    return weights, secs, float(losses[:m].mean()), float(losses[-m:].mean())
+    return weights, secs, float(losses[:m].mean()), float(losses[-m:].mean()), m, N
 
 
 PRECONDS = {"jacobi": "PRECOND_JACOBI", "fsai": "PRECOND_FSAI", "fsai_learned": "PRECOND_FSAI_LEARNED"}
+LEARNED_VARIANTS = [("learned_mixed", "fsai_learned", 1), ("learned_fp64", "fsai_learned", 0),
+                    ("classical_mixed", "fsai", 1), ("classical_fp64", "fsai", 0),
+                    ("jacobi_mixed", "jacobi", 1), ("jacobi_fp64", "jacobi", 0)]
+
+
+def learned_block(lib, h, dev, stream, weights, train_info, nops):
+    """Learned FSAI against Jacobi and classical FSAI, each in the mixed and the
+    plain FP64 path, on `nops` held-out anisotropic 128^3 operators (seeds
+    2000...): per variant the mean seconds per solve (CUDA events on the
+    handle's stream, inputs in HBM, the preconditioner's set-up inside each
+    solve), matvecs and cycles, the largest final residual, and the largest
+    eigenvalue spread against the plain FP64 Jacobi solve of the same operator
+    (and, where the oracle's run is stored, against the oracle)."""
+    import numpy as np
+    import torch
+    from paper_1711_10128_gb300 import workloads as W
+    w = WORKLOADS["aniso128"]
+    N, p = w["N"], w["p"]
+    ev_d = torch.zeros(p, dtype=torch.float64, device=dev)
+    X_d = torch.zeros((p, N ** 3), dtype=torch.float64, device=dev)
+    r_d = torch.zeros(p, dtype=torch.float64, device=dev)
+    oracle_ref = stored_oracle_run("aniso128")
+
+    def solve(Ad, precond, mixed):
+        prm = lib.make_params(w["p"], w["q"], w["k"], w["l"], w["tol"], 5000, w["seed"],
+                              getattr(lib, PRECONDS[precond]),
+                              lib.PRECISION_MIXED if mixed else lib.PRECISION_FP64, 1, 0.0,
+                              weights if precond == "fsai_learned" else None, (N, N, N), 1)
+        info = lib.trplk_info()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = lib.trplk_solve(h, Ad, None, prm, None, ev_d, X_d, r_d, info)
+        e1.record(stream)
+        e1.synchronize()
+        if rc != lib.OK:
+            raise RuntimeError(f"learned block: {precond} mixed={mixed} did not converge: {info.as_dict()}")
+        return e0.elapsed_time(e1) / 1e3, info.as_dict(), ev_d.cpu().numpy().copy()
+
+    rows = {name: [] for name, _, _ in LEARNED_VARIANTS}
+    for i, seed in enumerate(HELD_OUT_SEEDS[:nops]):
+        A = W.anisotropic_diffusion(N, seed)
+        t = (torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.col).to(dev), torch.from_numpy(A.val).to(dev))
+        Ad = lib.make_csr(*t)
+        if i == 0:   # warm-up: module loading, first allocations
+            for _, pc, mx in LEARNED_VARIANTS:
+                solve(Ad, pc, mx)
+        res = {}
+        for name, pc, mx in LEARNED_VARIANTS:
+            res[name] = solve(Ad, pc, mx)
+        base = res["jacobi_fp64"][2]
+        for name, (sec, info, ev) in res.items():
+            row = {"seed": seed, "seconds": sec, "mv_A": info["mv_A"], "cycles": info["cycles"],
+                   "refine_cycles": info["refine_cycles"], "max_resid": info["max_resid"],
+                   "eig_spread_vs_jacobi_fp64": float(np.max(np.abs(ev - base) / np.abs(base)))}
+            if seed == 2000 and oracle_ref is not None:
+                row["eig_err_vs_oracle"] = eig_error(ev, oracle_ref)
+            rows[name].append(row)
+        del Ad, t
+    summary = {}
+    for name, rr in rows.items():
+        summary[name] = {"mean_seconds": statistics.mean(r["seconds"] for r in rr),
+                         "mean_mv_A": statistics.mean(r["mv_A"] for r in rr),
+                         "mean_cycles": statistics.mean(r["cycles"] for r in rr),
+                         "max_resid": max(r["max_resid"] for r in rr),
+                         "max_eig_spread_vs_jacobi_fp64": max(r["eig_spread_vs_jacobi_fp64"] for r in rr)}
+        if any("eig_err_vs_oracle" in r for r in rr):
+            summary[name]["eig_err_vs_oracle_seed2000"] = next(r["eig_err_vs_oracle"] for r in rr
+                                                               if "eig_err_vs_oracle" in r)
+    jf = summary["jacobi_fp64"]["mean_seconds"]
+    out = {"family": "anisotropic 7-point diffusion 128^3 (axis factors loguniform[1, 100], coefficients "
+                     "lognormal(0, 1.5)), p = 20, q = 50, p_hat = 25, +K = 1, tol 1e-8",
+           "held_out_seeds": HELD_OUT_SEEDS[:nops], "training": train_info, "summary": summary,
+           "speedup_learned_mixed_vs_jacobi_fp64": jf / summary["learned_mixed"]["mean_seconds"],
+           "speedup_learned_mixed_vs_learned_fp64": summary["learned_fp64"]["mean_seconds"]
+           / summary["learned_mixed"]["mean_seconds"],
+           "matvec_gain_learned_vs_jacobi": summary["jacobi_fp64"]["mean_mv_A"] / summary["learned_fp64"]["mean_mv_A"],
+           "per_operator": rows}
+    return out
 
 
 def run_ours(args, world, rank, local, pg):
@@ -328,16 +440,20 @@ def run_ours(args, world, rank, local, pg):
     ev_d = torch.zeros(p, dtype=torch.float64, device=dev)
     X_d = torch.zeros((p, n), dtype=torch.float64, device=dev)
     r_d = torch.zeros(p, dtype=torch.float64, device=dev)
+    oracle_ref = stored_oracle_run(P["key"])
 
     setup = {}
     weights, grid = None, (0, 0, 0)
+    train_info = None
+    if P["precond"] == "fsai_learned" or args.learned_ops > 0:
+        weights, tsec, l0, l1, nops, tN = train_learned_fsai(lib, h, dev)
+        train_info = {"train_seconds": tsec, "train_ops": nops, "train_grid": tN, "train_loss_first": l0,
+                      "train_loss_last": l1, "adam_steps": 20 * nops,
+                      "note": "training is a one-off offline cost, outside every timed solve; the G build "
+                              "(features, MLP, pattern) runs inside each timed solve"}
     if P["precond"] == "fsai_learned":
-        weights, tsec, l0, l1 = train_learned_fsai(lib, h, dev)
         grid = (P["N"],) * 3
-        setup = {"train_seconds": tsec, "train_ops": len(P["train_seeds"]), "train_grid": P["train_N"],
-                 "train_loss_first": l0, "train_loss_last": l1,
-                 "note": "training is a one-off offline cost, outside every timed solve; the G build "
-                         "(features, MLP, pattern) runs inside each timed solve"}
+        setup = train_info
 
     def params(precision, precond, on_device):
         return lib.make_params(P["p"], P["q"], P["k"], P["l"], P["tol"], 5000, P["seed"],
@@ -381,6 +497,7 @@ def run_ours(args, world, rank, local, pg):
     # headline: mixed path, inputs resident in HBM, no profiler in the timed loop
     ms_mixed, infos, _, clocks = timed(lib.PRECISION_MIXED, P["precond"], args.steps, args.warmup)
     ms_mixed = max_over_ranks(pg, ms_mixed, local)
+    ev_mixed = ev_d.cpu().numpy().copy()
     # the same solves again with every launch bracketed by CUDA events on the
     # handle's stream: per-kernel durations for the roofline and the shares
     ms_prof, _, prof, _ = timed(lib.PRECISION_MIXED, P["precond"], args.steps, 0, profile=True)
@@ -390,6 +507,13 @@ def run_ours(args, world, rank, local, pg):
     info = infos[-1]
     out["solve"] = {k: info[k] for k in ("cycles", "refine_cycles", "mv_A", "mv_B", "prec_apply", "nconv",
                                          "max_resid")}
+    out["eig_err_vs_oracle"] = {"mixed": eig_error(ev_mixed, oracle_ref),
+                                "oracle_run": P["key"] if oracle_ref else None,
+                                "oracle_tol": oracle_ref["tol"] if oracle_ref else None,
+                                "note": "largest relative eigenvalue difference against the oracle's stored "
+                                        "converged FP64 run of this workload (oracle/reference_runs.json); the "
+                                        "FP64 path follows the oracle's arithmetic, the mixed path another "
+                                        "trajectory to the same residual"}
     out["gpu_launches"] = int(sum(i["launches"] for i in infos))
     out["profiled_ms_per_step"] = ms_prof
     out["clocks"] = clocks
@@ -407,7 +531,7 @@ def run_ours(args, world, rank, local, pg):
         achieved = by / (tms / 1e3) / 1e9
         out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                            "frac": achieved / hbm_peak, "peak_source": peak_src,
-                           "traffic": traffic_for(dom, by / nl) if P["key"] == "diffusion128" else None,
+                           "traffic": traffic_for(P["key"], dom, by / nl),
                            "launches": nl, "avg_launch_us": tms * 1e3 / nl,
                            "algorithmic_bytes_per_launch": by / nl}
     tot = sum(v[1] for v in prof.values()) or 1.0
@@ -432,10 +556,12 @@ def run_ours(args, world, rank, local, pg):
             ms, inf, _, _ = timed(prec, pc, max(1, args.steps) if name == "fp64" else 1, 1)
             ms = max_over_ranks(pg, ms, local)
             comp[name] = {"seconds": ms / 1e3, "cycles": inf[-1]["cycles"], "mv_A": inf[-1]["mv_A"],
-                          "max_resid": inf[-1]["max_resid"]}
+                          "max_resid": inf[-1]["max_resid"],
+                          "eig_err_vs_oracle": eig_error(ev_d.cpu().numpy(), oracle_ref)}
         out["fp64_seconds"] = comp["fp64"]["seconds"]
         out["fp64_cycles"] = fp64_cycles = comp["fp64"]["cycles"]
         out["speedup_vs_fp64"] = comp["fp64"]["seconds"] * 1e3 / ms_mixed
+        out["eig_err_vs_oracle"]["fp64"] = comp["fp64"]["eig_err_vs_oracle"]
         if len(comp) > 1:
             out["comparisons"] = comp
 
@@ -462,9 +588,14 @@ def run_ours(args, world, rank, local, pg):
             if i >= 1:
                 ts.append(time.perf_counter() - t0)
         e2e = max_over_ranks(pg, statistics.mean(ts), local)
-        h2d = hA + hB + (weights.nbytes if weights is not None else 0)
+        h2d = hA + hB + (weights.nbytes if (weights is not None and P["precond"] == "fsai_learned") else 0)
         d2h = ev_h.numel() * 8 + X_h.numel() * 8 + r_h.numel() * 8
         out["e2e"] = {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        out["eig_err_vs_oracle"]["e2e"] = eig_error(ev_h.numpy(), oracle_ref)
+
+    # the learned preconditioner on held-out operators of its family
+    if args.learned_ops > 0:
+        out["learned"] = learned_block(lib, h, dev, stream, weights, train_info, args.learned_ops)
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -212,7 +212,10 @@ trplk_status trplk_cgs2(trplk_handle* h, int dtype, int64_t n, int64_t ld, int w
  * T'): T double, column-major (ldT), only the upper triangle is read.
  * theta: double[w] ascending; Y: double w x w column-major (ld = w), each
  * column signed so its largest-magnitude entry (first such) is positive.
- * Cyclic Jacobi in one CTA, FP64.  w <= 64. */
+ * One CTA: cyclic Jacobi sweeps in FP32, two FP64 Newton-Schulz steps that
+ * make the accumulated rotations orthogonal to FP64 rounding, then FP64
+ * Jacobi sweeps on the rotated T until its off-diagonal norm is below
+ * 3e-15 ||T||_F (FP64 accuracy).  w <= 64. */
 trplk_status trplk_rayleigh_ritz(trplk_handle* h, int w, const double* T, int ldT, double* theta,
                                  double* Y);
 
@@ -259,9 +262,24 @@ trplk_status trplk_check_residuals(trplk_handle* h, const trplk_csr* A, const tr
  * must start at zero); calls whose kernels overlap on the GPU race on it and
  * must be serialised by the caller.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  No cudaMalloc, cudaFree or other allocating call. */
+ * any stream capture.  No cudaMalloc, cudaFree or other allocating call.
+ * Module loading: when the CUDA runtime loads modules lazily (its default
+ * since CUDA 12.2), the first call on each device is what loads this part of
+ * the library, and that load places the array (256 KiB) and the kernels'
+ * code in device memory.  Make the first call before the caller's own pool
+ * reserves the device's free memory, or set CUDA_MODULE_LOADING=EAGER so the
+ * load happens when the context is created; later calls load nothing. */
 trplk_status trplk_project_noalloc(int dtype, int64_t n, int64_t ld, int w, const void* BU,
                                    const void* v, double* hout, void* cuda_stream);
+
+/* Failure-injection hook for tests (not part of the method).  Every
+ * mbarrier wait of the streaming passes on this handle gives up after
+ * `polls` polls: polls = 0 makes each wait give up at once, so the next call
+ * that runs such a pass returns TRPLK_ETIMEOUT; polls < 0 restores the
+ * default (2^22 polls).  A pass that gives up waits until every bulk copy it
+ * issued has landed before its CTAs exit, so the handle stays usable.
+ * EINVAL for a NULL handle. */
+trplk_status trplk_set_wait_limit(trplk_handle* h, int64_t polls);
 
 /* ------------------------------------------------------------------------
  * Learned FSAI preconditioner (not in the paper: the data-parallel

@@ -35,6 +35,15 @@ F5 Loss over solver vectors v (columns of V): the energy-norm error of Mv as
    E_v = (Mv)^T A (Mv) - 2 ||Gv||^2 = ||A^-1 v - Mv||_A^2 - v^T A^-1 v,
    scaled by c_v = 1/(v^T D^-1 v) (D = diag A) and averaged over v; plus
    gamma = 0.1 times the Kaporin measure K(G).
+F6 BF16 mode (quant="bf16"): the network of F4 with the features (first
+   rounded to FP32), the weight matrices W1, W2, W3 and both hidden
+   activations rounded to bfloat16 (round to nearest, ties to even, through
+   FP32), everything else in FP64; biases are not rounded.  Its backward is
+   the F4/F5 chain rule evaluated at the rounded values (the rounding has zero
+   derivative almost everywhere, so this is the gradient the rounded network
+   is trained with).  Pins: the rounding against a library's bfloat16
+   conversion; the gradient with respect to b3, on which the rounded loss
+   depends smoothly, against finite differences.
 """
 from __future__ import annotations
 
@@ -111,13 +120,34 @@ def init_mlp(seed=0, hidden=64):
     return dict(W1=W1, b1=b1, W2=W2, b2=b2, W3=W3, b3=b3)
 
 
-def mlp_forward(p, F):
-    """o = W3 relu(W2 relu(W1 f + b1) + b2) + b3 for every row (F4)."""
-    z1 = F @ p["W1"].T + p["b1"]
-    h1 = np.maximum(z1, 0.0)
-    z2 = h1 @ p["W2"].T + p["b2"]
-    h2 = np.maximum(z2, 0.0)
-    o = h2 @ p["W3"].T + p["b3"]
+def bf16_round(x):
+    """x rounded to bfloat16 (F6): to FP32 first (nearest), then to the nearest
+    value with 8 significant bits, ties to even, returned as float64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float64).astype(np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _quantiser(quant):
+    if quant is None:
+        return lambda x: x
+    if quant == "bf16":
+        return bf16_round
+    raise ValueError(f"unknown quantisation {quant!r}")
+
+
+def mlp_forward(p, F, quant=None):
+    """o = W3 relu(W2 relu(W1 f + b1) + b2) + b3 for every row (F4); with
+    quant = "bf16" the features, W1..W3 and the hidden activations are
+    rounded to bfloat16 (F6)."""
+    q = _quantiser(quant)
+    F = q(F)
+    z1 = F @ q(p["W1"]).T + p["b1"]
+    h1 = q(np.maximum(z1, 0.0))
+    z2 = h1 @ q(p["W2"]).T + p["b2"]
+    h2 = q(np.maximum(z2, 0.0))
+    o = h2 @ q(p["W3"]).T + p["b3"]
     return o, (F, z1, h1, z2, h2)
 
 
@@ -185,11 +215,13 @@ def loss_and_grad_G(G, A, V):
     return E + GAMMA * K, gE + GAMMA * gK, dict(E=E, K=K)
 
 
-def loss_and_grad_mlp(p, A, dims, V):
-    """Loss of the MLP-predicted G and the gradient w.r.t. every weight (F4, F5)."""
+def loss_and_grad_mlp(p, A, dims, V, quant=None):
+    """Loss of the MLP-predicted G and the gradient w.r.t. every weight (F4, F5;
+    F6 with quant = "bf16")."""
     A = sp.csr_matrix(A)
+    q = _quantiser(quant)
     F = features_7pt(A, dims)
-    o, (F_, z1, h1, z2, h2) = mlp_forward(p, F)
+    o, (F_, z1, h1, z2, h2) = mlp_forward(p, F, quant)
     G = g_from_outputs(A, dims, o)
     L, gG, parts = loss_and_grad_G(G, A, V)
     # dL/do from dL/dG (F4 chain rule)
@@ -211,11 +243,11 @@ def loss_and_grad_mlp(p, A, dims, V):
     g = {}
     g["W3"] = dO.T @ h2
     g["b3"] = dO.sum(axis=0)
-    dh2 = dO @ p["W3"] * (z2 > 0)
+    dh2 = dO @ q(p["W3"]) * (z2 > 0)
     g["W2"] = dh2.T @ h1
     g["b2"] = dh2.sum(axis=0)
-    dh1 = dh2 @ p["W2"] * (z1 > 0)
-    g["W1"] = dh1.T @ F
+    dh1 = dh2 @ q(p["W2"]) * (z1 > 0)
+    g["W1"] = dh1.T @ F_
     g["b1"] = dh1.sum(axis=0)
     return L, g, parts
 

@@ -28,6 +28,10 @@ def workloads():
         # 3D 7-point lognormal(0,1) diffusion on 128^3, 10 smallest, Jacobi, q=40, p_hat=15, +K=1, tol 1e-8
         "diffusion128": dict(build=lambda: (W.diffusion_3d(128, W.lognormal_field(128, 1.0, 1)), None),
                              p=10, q=40, k=15, l=1, tol=1e-8, seed=0),
+        # the 128^3 diffusion operator above at tol 1e-12: there the Kato-Temple bound of every pair falls
+        # below 1e-10 relative, so the eigenvalues of any two converged runs compare at 1e-10
+        "diffusion128_tight": dict(build=lambda: (W.diffusion_3d(128, W.lognormal_field(128, 1.0, 1)), None),
+                                   p=10, q=40, k=15, l=1, tol=1e-12, seed=0),
         # 2D 5-point Laplacian on 100x100, 5 smallest, Jacobi, q=20, p_hat=8, +K=5, tol 1e-8
         "laplace100": dict(build=lambda: (W.laplacian_2d(100), None), p=5, q=20, k=8, l=5, tol=1e-8, seed=0),
         # Q1 stiffness/mass pencil on 96^3 elements, E ~ U[1,10] (seed 2), 20 smallest, q=50, p_hat=25, +K=1

@@ -82,6 +82,7 @@ def _load():
         "trplk_start_block": (st, [vp, i64, i64, i32, C.c_uint64, vp]),
         "trplk_check_residuals": (st, [vp, C.POINTER(trplk_csr), C.POINTER(trplk_csr), i64, i32, vp, vp, dbl, vp]),
         "trplk_project_noalloc": (st, [i32, i64, i64, i32, vp, vp, vp, vp]),
+        "trplk_set_wait_limit": (st, [vp, i64]),
         "trplk_mlp_param_count": (C.c_int, []),
         "trplk_fsai_mlp_init": (st, [vp, C.c_uint64]),
         "trplk_fsai_values": (st, [vp, C.POINTER(trplk_csr), i32, vp, vp, i32, vp, C.POINTER(C.c_int64)]),
@@ -232,6 +233,12 @@ def trplk_project_noalloc(dtype, n, ld, w, BU, v, hout, stream=None):
     if rc != OK:
         raise TrplkError(rc, "trplk_project_noalloc failed")
     return rc
+
+
+def trplk_set_wait_limit(h, polls):
+    """Failure-injection hook: bound the streaming passes' waits to `polls`
+    polls (0: give up at once; negative: the default)."""
+    return h.check(LIB.trplk_set_wait_limit(h.h, int(polls)))
 
 
 def trplk_fsai_values(h, A, kind, dims=None, weights=None, bf16=0, g=None):

@@ -24,7 +24,15 @@ enum : int {
   kFlagBreakdown = 4,   // Lanczos vector fell into the span of the basis
   kFlagNotSPD = 8,      // x^T B x <= 0 seen
   kFlagJacobi = 16,     // Rayleigh-Ritz eigensolver did not converge
+  kFlagDrain = 32,      // after a timeout, an issued bulk copy did not land within kDrainPolls
 };
+
+// Polls of one bounded mbarrier wait in the streaming passes (the default;
+// a handle may lower it to exercise the timeout path), and of the wait for
+// the copies still in flight when a CTA gives up.  Copies from valid device
+// memory always land, so the second bound is a backstop only.
+constexpr uint32_t kWaitPolls = 1u << 22;
+constexpr uint32_t kDrainPolls = 1u << 26;
 
 // Storage traits.  Rows are tiled in TR-row tiles; a CTA has TR threads so a
 // thread owns one row of a tile.  One tile column is TR * sizeof(S) = 1 KiB.
@@ -207,9 +215,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait: gives up after `limit` polls (each poll itself suspends for a
 // hardware-chosen time) and reports false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit = 1u << 22) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit = kWaitPolls) {
   for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+  }
+  return false;
+}
+
+// Warp-uniform bounded wait: every lane polls until all lanes have seen the
+// phase complete (true), any lane sees *abort set, or `limit` rounds have
+// passed (false).  All lanes leave after the same round with the same result,
+// so the warp stays converged whether the wait succeeds or gives up.  A
+// completed phase stays visible until the waiting warp itself releases the
+// stage, so a lane that has seen it need not poll again.
+__device__ __forceinline__ bool mbar_warp_wait(uint64_t* bar, uint32_t parity, uint32_t limit,
+                                               const volatile int* abort) {
+  bool done = false;
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (!done) done = mbar_try_wait(bar, parity);
+    if (__all_sync(0xffffffffu, done)) return true;
+    if (__any_sync(0xffffffffu, *abort != 0)) return false;
   }
   return false;
 }

@@ -57,6 +57,7 @@ struct Ctx {
   unsigned int* counter = nullptr; // last-CTA ticket, kept at zero between kernels
   int* status = nullptr;           // device status word (kFlag*)
   Profiler* prof = nullptr;
+  uint32_t wait_polls = kWaitPolls;  // bound of the streaming passes' mbarrier waits
 };
 
 // RAII bracket of one kernel launch for the profiler.

@@ -21,7 +21,12 @@
 //
 // The device address of the array is looked up once per device, on the first
 // call with that device current (cudaGetSymbolAddress); make that first call
-// before any stream capture begins.
+// before any stream capture begins.  Under lazy module loading (the CUDA
+// runtime's default since 12.2) that first call is also what loads this
+// file's module, and the load places the array and the kernels' code in
+// device memory: the first call must come before the caller's pool takes the
+// device's free memory (or the process runs with CUDA_MODULE_LOADING=EAGER).
+// Later calls allocate nothing.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -60,6 +65,36 @@ trplk_status scratch_address(int dev, double** out) {
 }
 
 constexpr size_t kSmemMax = 232448 - 1024;
+constexpr size_t kSmemPerSM = 233472;
+
+// One launch of the projection kernel instantiated for bases of at most MAXW
+// columns (narrower instantiations keep their accumulators in registers).
+template <typename S, int MAXW>
+trplk_status launch_project(TSArgs<S>& a, cudaStream_t stream, int sms) {
+  constexpr int TR = Tile<S>::TR;
+  constexpr int kThreads = TR + 32;
+  auto kern = ts_kernel<S, TS_PROJ, MAXW>;
+  const size_t fixed = ts_smem_fixed<S>(0);
+  const size_t stage = ts_stage_bytes<S>(1, a.w, 1);
+  const int stages = (int)std::min<size_t>(4, (kSmemMax - fixed) / stage);
+  if (stages < 1) return TRPLK_EINVAL;
+  a.stages = stages;
+  const size_t smem = fixed + (size_t)stages * stage;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax) != cudaSuccess) {
+    cudaGetLastError();
+    return TRPLK_ECUDA;
+  }
+  // CTAs per SM: the fewest allowed by shared memory, registers and threads
+  const int by_smem = (int)std::max<size_t>(1, kSmemPerSM / (smem + 1024));
+  const int by_regs = std::max(1, 65536 / (std::max(fa.numRegs, 1) * kThreads));
+  const int per_sm = std::min(std::min(by_smem, by_regs), 2048 / kThreads);
+  int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)sms * per_sm);
+  grid = std::min(grid, kNoAllocCtas);
+  kern<<<grid, kThreads, smem, stream>>>(a);
+  return cudaGetLastError() == cudaSuccess ? TRPLK_OK : TRPLK_ECUDA;
+}
 
 template <typename S>
 trplk_status project_noalloc(int64_t ld, int w, const S* BU, const S* v, double* hout, cudaStream_t stream,
@@ -75,34 +110,30 @@ trplk_status project_noalloc(int64_t ld, int w, const S* BU, const S* v, double*
   a.ld = ld;
   a.out0 = hout;
   a.ntiles = (int)(ld / TR);
-  const size_t fixed = ts_smem_fixed<S>(0);
-  const size_t stage = ts_stage_bytes<S>(1, w, 1);
-  const int stages = (int)std::min<size_t>(4, (kSmemMax - fixed) / stage);
-  if (stages < 1) return TRPLK_EINVAL;
-  a.stages = stages;
-  const size_t smem = fixed + (size_t)stages * stage;
   a.partials = scratch;
   a.pstride = kPartialStride;
   a.counter = reinterpret_cast<unsigned int*>(scratch + kPartialDoubles);
   a.status = reinterpret_cast<int*>(scratch + kPartialDoubles + 1);
+  a.polls = kWaitPolls;
   a.kind = TS_PROJ;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();
     return TRPLK_ECUDA;
   }
-  const int per_sm = (int)std::max<size_t>(1, 233472 / (smem + 1024));
-  int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)sms * std::min(per_sm, 2048 / (TR + 32)));
-  grid = std::min(grid, kNoAllocCtas);
   // ticket and status start at zero on every call (the array keeps old contents)
-  if (cudaMemsetAsync(scratch + kPartialDoubles, 0, 32 * sizeof(double), stream) != cudaSuccess ||
-      cudaFuncSetAttribute(ts_kernel<S, TS_PROJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax) !=
-          cudaSuccess) {
+  if (cudaMemsetAsync(scratch + kPartialDoubles, 0, 32 * sizeof(double), stream) != cudaSuccess) {
     cudaGetLastError();
     return TRPLK_ECUDA;
   }
-  ts_kernel<S, TS_PROJ><<<grid, TR + 32, smem, stream>>>(a);
-  if (cudaGetLastError() != cudaSuccess) return TRPLK_ECUDA;
+  trplk_status st;
+  if (w <= kMaxQ / 2)
+    st = launch_project<S, kMaxQ / 2>(a, stream, sms);
+  else if (w <= 3 * kMaxQ / 4)
+    st = launch_project<S, 3 * kMaxQ / 4>(a, stream, sms);
+  else
+    st = launch_project<S, kMaxQ>(a, stream, sms);
+  if (st != TRPLK_OK) return st;
   int flags = 0;
   if (cudaMemcpyAsync(&flags, a.status, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
       cudaStreamSynchronize(stream) != cudaSuccess) {

@@ -191,7 +191,10 @@ void check_flags(trplk_handle* h, int mask_ignore = kFlagBreakdown) {
   if (f) {
     trplk_status s = status_from_flags(f);
     if (s == TRPLK_OK) s = TRPLK_ECUDA;
-    throw Error(s, "device status flags 0x" + std::to_string(f));
+    std::string m = "device status flags 0x" + std::to_string(f);
+    if (f & kFlagTimeout) m += " (a bounded mbarrier wait gave up)";
+    if (f & kFlagDrain) m += " (a bulk copy had not landed when its CTA gave up waiting for it)";
+    throw Error(s, m);
   }
 }
 
@@ -1046,6 +1049,14 @@ trplk_status trplk_check_residuals(trplk_handle* h, const trplk_csr* A, const tr
     check_residuals_fp64(h, Aop, B ? &Bop : nullptr, ld, p, X, theta, normA, rh.data());
     TRPLK_CUDA_TRY(cudaMemcpy(resid, rh.data(), p * sizeof(double), cudaMemcpyHostToDevice));
     check_flags(h, 0);
+    return TRPLK_OK;
+  });
+}
+
+trplk_status trplk_set_wait_limit(trplk_handle* h, int64_t polls) {
+  return guarded(h, [&]() -> trplk_status {
+    h->sync();
+    h->ctx.wait_polls = polls < 0 ? kWaitPolls : (uint32_t)std::min<int64_t>(polls, 1ll << 31);
     return TRPLK_OK;
   });
 }

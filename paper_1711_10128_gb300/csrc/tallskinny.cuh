@@ -22,8 +22,13 @@
 //    are reduced per CTA and then summed in CTA order by the last CTA to
 //    finish (deterministic, no floating-point atomics).
 // Rows n..ld-1 of every array are zero, so whole tiles are always copied.
-// Every wait is bounded: a stage that never arrives sets kFlagTimeout, the
-// kernel drains the copies it issued and returns.
+// Every wait is bounded (a.polls polls) and also ends when another warp of
+// the CTA has given up (a flag in shared memory); every wait's outcome is
+// warp-uniform, and the consumer warps of TS_UPDPROJ, which meet at a named
+// barrier once per tile, decide together at that barrier.  A CTA that gives
+// up sets kFlagTimeout, waits until every bulk copy it issued has landed (so
+// no copy writes into the shared memory of an exited CTA), still takes part
+// in the grid reduction's ticket, and returns; the host reads the flag.
 #pragma once
 #include <type_traits>
 
@@ -97,6 +102,7 @@ struct TSArgs {
   double* scale_out;     // 1/beta for UPDNORM / DOT
   double eps_breakdown;
   int* status;           // device status word (flags)
+  uint32_t polls;        // bound of every mbarrier wait (kWaitPolls unless lowered for a test)
 };
 
 // Row slices per tile for the projection tasks: a task is (column, slice)
@@ -160,6 +166,20 @@ __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory");
 }
 
+// Named barrier 1 over the consumer threads that also ORs a predicate across
+// them: true in every consumer thread if any passed `flag` != 0.
+template <int NTHREADS>
+__device__ __forceinline__ bool consumer_sync_or(bool flag) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, 1, %2, pi;\n"
+      " selp.u32 %0, 1, 0, po;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)flag), "n"(NTHREADS)
+      : "memory");
+  return r != 0;
+}
+
 // Two CTAs per SM for the float path (<= 113 registers), where the FP32
 // pipes need the extra warps to hide the compensated-sum latency chains.
 template <typename S> struct MinBlocks { static constexpr int value = 1; };
@@ -203,7 +223,9 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
     }
   if (KIND == TS_RESID)
     for (int j = tid; j < a.k; j += blockDim.x) s_y[j] = (S)a.theta[j];
+  __shared__ int s_abort;   // set by the first warp that gives up a wait
   if (tid == 0) {
+    s_abort = 0;
     for (int s = 0; s < a.stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NW);
@@ -211,6 +233,7 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
     fence_mbar_init();
   }
   __syncthreads();
+  volatile int* abort_flag = &s_abort;
 
   const int my_tiles = (a.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   // TS_INNER's second right-hand side is the first CGS pass: plain
@@ -231,9 +254,20 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
       const int s = it % a.stages;
       if (it >= a.stages) {
         int ok = 1;
-        if (lane == 0) ok = mbar_wait_bounded(&empty[s], (uint32_t)(((it / a.stages) - 1) & 1)) ? 1 : 0;
+        if (lane == 0) {
+          ok = 0;
+          const uint32_t par = (uint32_t)(((it / a.stages) - 1) & 1);
+          for (uint32_t i = 0; i < a.polls; ++i) {
+            if (mbar_try_wait(&empty[s], par)) { ok = 1; break; }
+            if (*abort_flag) break;
+          }
+        }
         ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) { fail = true; break; }
+        if (!ok) {
+          if (lane == 0) *abort_flag = 1;
+          fail = true;
+          break;
+        }
       }
       ts_issue_tile(a, stages + s * stage_bytes, &full[s], blockIdx.x + it * gridDim.x, lane);
       issued_upto = it + 1;
@@ -242,7 +276,15 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
     // ---------------- consumer warps
     for (int it = 0; it < my_tiles; ++it) {
       const int s = it % a.stages;
-      if (!mbar_wait_bounded(&full[s], (uint32_t)((it / a.stages) & 1))) { fail = true; break; }
+      const bool ok = mbar_warp_wait(&full[s], (uint32_t)((it / a.stages) & 1), a.polls, abort_flag);
+      if (!ok) {
+        if (lane == 0) *abort_flag = 1;
+        // TS_UPDPROJ's consumers meet at a named barrier in every tile: a
+        // warp that gave up still goes there once, where all of them learn it
+        if (KIND == TS_UPDPROJ) consumer_sync_or<TR>(true);
+        fail = true;
+        break;
+      }
       const int tile = blockIdx.x + it * gridDim.x;
       const int64_t row0 = (int64_t)tile * TR;
       const S* st = reinterpret_cast<const S*>(stages + s * stage_bytes);
@@ -351,7 +393,9 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
         if (KIND == TS_UPDNORM) racc.fma(vn, vn);
         if (KIND == TS_UPDPROJ) {
           s_v[tid] = vn;
-          consumer_sync<TR>();
+          // the tile's barrier; it also tells every consumer whether another
+          // consumer warp gave up its wait for this tile
+          if (consumer_sync_or<TR>(false)) { fail = true; break; }
           V4<S> vq[NQ];
 #pragma unroll
           for (int h = 0; h < NQ; ++h) vq[h] = ld4(s_v + h * SLICE + 4 * lane);
@@ -402,14 +446,22 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
     }
   }
 
-  // ---------------- drain and report a timeout
-  if (fail) atomicOr(a.status, kFlagTimeout);
-  if (producer && fail) {
-    // copies issued but possibly still in flight into our shared memory
-    for (int it = issued_upto - a.stages; it < issued_upto; ++it) {
-      if (it < 0) continue;
-      const int s = it % a.stages;
-      if (lane == 0) mbar_wait_bounded(&full[s], (uint32_t)((it / a.stages) & 1));
+  // ---------------- agree on a timeout, drain, report
+  // Tiles older than issued_upto - stages have landed: the producer issued
+  // each later tile only after every consumer warp had released the older
+  // one's stage, which it did after seeing that tile's full barrier complete.
+  // The last `stages` issued tiles may still be in flight.
+  if (fail) *abort_flag = 1;
+  __syncthreads();
+  if (*abort_flag) {
+    if (tid == 0) atomicOr(a.status, kFlagTimeout);
+    if (producer && lane == 0) {
+      for (int it = issued_upto - a.stages; it < issued_upto; ++it) {
+        if (it < 0) continue;
+        const int s = it % a.stages;
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((it / a.stages) & 1), kDrainPolls))
+          atomicOr(a.status, kFlagDrain);
+      }
     }
   }
   __syncthreads();

@@ -86,6 +86,7 @@ void run(const Ctx& c, TSArgs<S> a, int kind) {
   a.pstride = kPartialStride;
   a.counter = c.counter;
   a.status = c.status;
+  a.polls = c.wait_polls;
   a.kind = kind;
   // algorithmic bytes: every staged column and vector once, plus the outputs
   double bytes = (double)(a.nmat * a.w + a.nvec) * a.ld * sizeof(S);

@@ -128,3 +128,46 @@ def test_classical_fsai_is_representable_by_the_output_map():
     o[:, 3] = np.log(np.expm1(1 / np.sqrt(1 - s)))
     G = F.g_from_outputs(A, (N, N, N), o)
     assert np.allclose(G.toarray(), F.classical_fsai(A).toarray(), atol=1e-12)
+
+
+def test_bf16_rounding_matches_the_library_conversion():
+    """F6's rounding (through FP32, nearest, ties to even) against torch's
+    float32 -> bfloat16 conversion, on random values of many magnitudes and on
+    exact ties (low 16 bits 0x8000) with both parities of the kept bit."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(20000) * np.exp(rng.uniform(-30, 30, 20000))
+    bits = rng.integers(0, 2 ** 31, 4000, dtype=np.uint64).astype(np.uint32)
+    ties = ((bits & np.uint32(0x7F7F0000)) | np.uint32(0x8000)).view(np.float32).astype(np.float64)
+    for v in (x, ties, -ties, np.array([0.0, 1.0, -2.5, 3.0e38, 1.0e-38])):
+        ref = torch.from_numpy(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+        assert np.array_equal(F.bf16_round(v), ref)
+
+
+def test_bf16_mode_b3_gradient_matches_finite_differences():
+    """The BF16 mode (F6): b3 is not rounded and enters after the last rounded
+    activation, so the rounded network's loss is smooth in b3 and its analytic
+    gradient must match central differences.  The BF16 loss stays within the
+    rounding's reach of the FP64 loss (8 significant bits: a few 2^-8)."""
+    dims = (4, 4, 4)
+    A = W.diffusion_3d(4, W.lognormal_field(4, 1.0, 8), axis=(1.0, 3.0, 9.0)).to_scipy()
+    p = F.init_mlp(4, hidden=8)
+    rng = np.random.default_rng(6)
+    p["W3"] = 0.1 * rng.standard_normal(p["W3"].shape)
+    p["b2"] = 0.1 * rng.standard_normal(p["b2"].shape)
+    V = rng.standard_normal((A.shape[0], 2))
+    L, g, _ = F.loss_and_grad_mlp(p, A, dims, V, quant="bf16")
+    for idx in range(4):
+        h = 1e-6
+        old = p["b3"][idx]
+        p["b3"][idx] = old + h
+        lp = F.loss_and_grad_mlp(p, A, dims, V, quant="bf16")[0]
+        p["b3"][idx] = old - h
+        lm = F.loss_and_grad_mlp(p, A, dims, V, quant="bf16")[0]
+        p["b3"][idx] = old
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g["b3"][idx]) <= 1e-5 * max(1.0, abs(fd)), (idx, fd, g["b3"][idx])
+    L64, g64, _ = F.loss_and_grad_mlp(p, A, dims, V)
+    assert L != L64 and abs(L - L64) <= 4 * 2.0 ** -8 * abs(L64)
+    for name in g:
+        assert np.all(np.abs(g[name] - g64[name]) <= 0.1 * np.abs(g64[name]).max() + 1e-300), name

@@ -63,3 +63,50 @@ def test_max_cycles_returns_not_converged_with_best_pairs(lib, h):
     assert info["cycles"] == 2 and info["nconv"] < 3
     assert np.all(np.isfinite(ev)) and np.all(np.diff(ev) >= 0) and np.all(np.isfinite(res))
     assert np.allclose(X.T @ X, np.eye(3), atol=1e-10)
+
+
+def test_wait_timeout_returns_etimeout_and_the_handle_recovers(lib, h):
+    """The bounded waits of the streaming passes, made to run out on purpose:
+    with the handle's wait limit at 0 polls every mbarrier wait gives up at
+    once.  The pass must agree on it across the CTA (the update-and-project
+    pass meets at a named barrier every tile), wait for the bulk copies it
+    already issued, return TRPLK_ETIMEOUT through the status word -- never a
+    hang or a fault -- and leave the handle usable: the same calls with the
+    default limit then give the definition's answers and a solve converges."""
+    n = 300_000   # 1172 FP32 tiles: more than the CTAs, several stages in flight per CTA
+    ld = (n + 255) // 256 * 256
+    w = 20
+    rng = np.random.default_rng(5)
+    U = np.linalg.qr(rng.standard_normal((n, w)))[0]
+    v = rng.standard_normal(n)
+    Ud = torch.zeros((w, ld), dtype=torch.float32, device="cuda")
+    Ud[:, :n] = torch.from_numpy(np.ascontiguousarray(U.T)).float().cuda()
+    vd = torch.zeros(ld, dtype=torch.float32, device="cuda")
+    vd[:n] = torch.from_numpy(v).float().cuda()
+    hout = torch.zeros(w, dtype=torch.float64, device="cuda")
+    beta = torch.zeros(2, dtype=torch.float64, device="cuda")
+    A = W.laplacian_2d(40)
+    lib.trplk_set_wait_limit(h, 0)
+    try:
+        with pytest.raises(lib.TrplkError) as e:
+            lib.trplk_project(h, lib.F32, n, ld, w, Ud, vd, hout)
+        assert e.value.code == lib.ETIMEOUT
+        with pytest.raises(lib.TrplkError) as e:      # update + projection, then update + norm
+            lib.trplk_cgs2(h, lib.F32, n, ld, w, Ud, Ud, None, hout, vd.clone(), None, beta)
+        assert e.value.code == lib.ETIMEOUT
+        for precision in (lib.PRECISION_FP64, lib.PRECISION_MIXED):
+            with pytest.raises(lib.TrplkError) as e:
+                lib.solve(h, dev_csr(lib, A), None, p=2, q=12, k=4, l=1, tol=1e-8, precision=precision)
+            assert e.value.code == lib.ETIMEOUT
+            assert "gave up" in lib.trplk_last_error(h)
+    finally:
+        lib.trplk_set_wait_limit(h, -1)
+    lib.trplk_project(h, lib.F32, n, ld, w, Ud, vd, hout)
+    Uf = Ud[:, :n].double().cpu().numpy()
+    vf = vd[:n].double().cpu().numpy()
+    ref = Uf @ vf
+    mag = np.abs(Uf) @ np.abs(vf)
+    assert np.all(np.abs(hout.cpu().numpy() - ref) <= 4 * 2.0 ** -24 * mag + 1e-13)
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), None, p=2, q=12, k=4, l=1, tol=1e-8,
+                                     precision=lib.PRECISION_MIXED)
+    assert rc == lib.OK and np.all(res <= 1e-8)
