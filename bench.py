@@ -537,6 +537,8 @@ def run_ours(args, world, rank, local, pg):
     tot = sum(v[1] for v in prof.values()) or 1.0
     out["kernel_time_share"] = {k: round(v[1] / tot, 4) for k, v in sorted(prof.items(), key=lambda x: -x[1][1])}
     out["kernel_gbs"] = {k: round(v[2] / (v[1] / 1e3) / 1e9, 1) for k, v in prof.items() if v[1] > 0 and v[2] > 0}
+    out["kernel_avg_us"] = {k: round(v[1] * 1e3 / v[0], 2) for k, v in prof.items() if v[0] > 0}
+    out["kernel_launches_per_step"] = {k: v[0] / max(1, args.steps) for k, v in prof.items()}
     for key in ("spmv_scaled", "spmv"):
         if key in prof and prof[key][1] > 0:
             nl, tms, by = prof[key]

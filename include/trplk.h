@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define TRPLK_ABI_VERSION 1
+#define TRPLK_ABI_VERSION 2
 
 typedef enum {
   TRPLK_OK = 0,
@@ -59,7 +59,16 @@ enum {
   TRPLK_PRECOND_NONE = 0,          /* M = I                                   */
   TRPLK_PRECOND_JACOBI = 1,        /* M = diag(A)^-1                          */
   TRPLK_PRECOND_FSAI = 2,          /* M = G^T G, classical FSAI on tril(A)    */
-  TRPLK_PRECOND_FSAI_LEARNED = 3   /* M = G^T G, G predicted by the MLP       */
+  TRPLK_PRECOND_FSAI_LEARNED = 3,  /* M = G^T G, G predicted by the MLP       */
+  TRPLK_PRECOND_JACOBI_SHIFTED = 4 /* M_i = diag(A - rho_i B)^-1, rebuilt every
+                                      cycle (Sec. 3: M may change per cycle to
+                                      approximate (A - rho_i B)^-1); each
+                                      diagonal entry floored at 1e-3 a_jj     */
+};
+enum {
+  TRPLK_LOCKING_SOFT = 0,  /* Algorithm 1: converged pairs stay in the basis   */
+  TRPLK_LOCKING_HARD = 1   /* converged pairs are locked out of the search
+                              (Sec. 3: hard locking can replace soft locking) */
 };
 
 /* Packed MLP parameters of the learned FSAI (FP32, this order):
@@ -107,7 +116,16 @@ typedef struct {
  *             120 cycles); FP64 cycles from its Ritz vectors then finish to
  *             tol -- each starting from the preconditioned residuals of all
  *             pairs within 100x of tol, basis min(q, k + p + 4 + l) -- and
- *             info.refine_cycles counts them                             */
+ *             info.refine_cycles counts them
+ *  locking    TRPLK_LOCKING_SOFT or _HARD.  Hard: after each Rayleigh-Ritz
+ *             step the leading run of converged pairs of the active basis is
+ *             locked; locked vectors keep their place at the front of the
+ *             basis (they count against q and k), every new basis vector is
+ *             B-orthogonalised against them, and T, the Rayleigh-Ritz step and
+ *             the restart cover the active columns only; the target is always
+ *             the smallest active pair; the solve ends when p pairs are
+ *             locked.  The mixed path locks in its FP32 phase; its FP64
+ *             refinement polishes all p pairs with soft locking.          */
 typedef struct {
   int p, q, k, l;
   double tol;
@@ -121,6 +139,7 @@ typedef struct {
   int grid[3];
   int mlp_bf16;
   double mixed_tol;
+  int locking;
 } trplk_params;
 
 /* Counters and timings of one solve. */
@@ -135,6 +154,7 @@ typedef struct {
   double normA;           /* ||A||_1                                          */
   double max_resid;       /* largest final relative residual                  */
   int64_t launches;       /* kernel launches of this call                     */
+  int locked;             /* pairs locked (hard locking; 0 with soft locking) */
 } trplk_info;
 
 /* Create a handle bound to CUDA device `device`.  cuda_stream: a

@@ -47,6 +47,25 @@ R9  Convergence: one target advance per cycle at most (the IF of
 R10 Restart: X = U Y(:, 1:p_hat) (likewise AX, BX), T = diag(theta_1..p_hat),
     rho = theta_t, first Lanczos vector u = M r_t.  M is fixed across cycles
     (Jacobi: M = diag(A)^-1; the paper builds its ILU on A, Sec. 5.4).
+R13 Hard locking (locking="hard"; Sec. 3 says it can replace the soft locking
+    of Algorithm 1 but does not spell it out): after a cycle's Rayleigh-Ritz
+    step, the leading run of converged Ritz pairs of the active basis is
+    locked -- their vectors move to a locked block Q (kept, never rotated
+    again), their Ritz values are final.  The locked vectors count against
+    the memory budget: with |Q| locked the active search uses basis
+    q - |Q|, restart size p_hat - |Q| and seeks the p - |Q| smallest pairs;
+    every new basis vector (Lanczos, restart and +K vectors) is
+    B-orthogonalised against [Q, U] by CGS2, while T and the Rayleigh-Ritz
+    step cover the active basis only.  The target is always the smallest
+    active pair; locking s pairs drops the first s columns of X_prev.  The
+    solve ends when p pairs are locked.  Outputs are sorted by value.  Each
+    cycle still costs q - p_hat matvecs, so the accounting of R6 holds.
+R14 Per-cycle preconditioner (precond="jacobi_shifted"; Sec. 3 notes that M
+    may change every cycle to approximate (A - rho_i B)^-1): the shifted
+    Jacobi preconditioner M_i = diag(d)^-1 with
+    d_j = max(a_jj - rho_i b_jj, 1e-3 a_jj), rebuilt at the start of every
+    cycle from that cycle's rho_i (the floor keeps M_i positive definite when
+    rho_i passes a diagonal ratio a_jj / b_jj).
 """
 from __future__ import annotations
 
@@ -77,6 +96,15 @@ def spmv(A, x):
 def jacobi_preconditioner(A):
     """M = diag(A)^-1 applied elementwise (reading R10)."""
     dinv = 1.0 / A.diagonal()
+    return lambda v: dinv * v
+
+
+def shifted_jacobi_preconditioner(A, B, rho):
+    """M_i = diag(max(a_jj - rho b_jj, 1e-3 a_jj))^-1 (reading R14)."""
+    a = A.diagonal()
+    b = np.ones_like(a) if B is None else B.diagonal()
+    d = np.maximum(a - rho * b, 1e-3 * a)
+    dinv = 1.0 / d
     return lambda v: dinv * v
 
 
@@ -158,22 +186,29 @@ def residual_norms(AX, BX, X, theta):
     return np.linalg.norm(R, axis=0), np.linalg.norm(X, axis=0)
 
 
-def solve(A, B, p, q, k, l, tol, X0, precond="jacobi", max_cycles=5000, record=False):
+def solve(A, B, p, q, k, l, tol, X0, precond="jacobi", max_cycles=5000, record=False, locking="soft"):
     """TRPL+K (Algorithm 1) for the p smallest eigenpairs of (A, B).
 
     A, B: scipy CSR (B None means identity); q: maximum basis size; k: thick
     restart size p_hat >= p; l: maximum number of +K vectors; X0: n x k start
-    block.  Returns a dict with evals, evecs (B-orthonormal), resid (final FP64
-    check with fresh matvecs, relative to ||A||_1 ||x||_2), status, cycles,
-    matvec counters and a per-cycle history.
+    block; precond: "jacobi", "none", "jacobi_shifted" (R14) or a function;
+    locking: "soft" (Algorithm 1) or "hard" (R13).  Returns a dict with
+    evals, evecs (B-orthonormal), resid (final FP64 check with fresh matvecs,
+    relative to ||A||_1 ||x||_2), status, cycles, matvec counters and a
+    per-cycle history.
     """
+    if locking == "hard":
+        return _solve_hard(A, B, p, q, k, l, tol, X0, precond, max_cycles, record)
+    if locking != "soft":
+        raise ValueError(f"unknown locking {locking!r}")
     A = sp.csr_matrix(A)
     n = A.shape[0]
     if not (1 <= p <= k and k + max(l, 1) + 1 <= q <= n):
         raise ValueError("need 1 <= p <= k and k + max(l,1) + 1 <= q <= n")
     Bm = None if B is None else sp.csr_matrix(B)
     applyB = (lambda x: x.copy()) if Bm is None else (lambda x: Bm @ x)
-    Mapply = make_preconditioner(A, precond)
+    shifted = precond == "jacobi_shifted"
+    Mapply = None if shifted else make_preconditioner(A, precond)
     normA = norm1(A)
     cnt = dict(mv_A=0, mv_B=0, prec=0, mv_check=0)
 
@@ -193,6 +228,8 @@ def solve(A, B, p, q, k, l, tol, X0, precond="jacobi", max_cycles=5000, record=F
     cycle = 0
     for cycle in range(1, max_cycles + 1):
         rho = theta[t]
+        if shifted:   # M_i from this cycle's shift (R14)
+            Mapply = shifted_jacobi_preconditioner(A, Bm, rho)
         U[:] = 0.0
         AU[:] = 0.0
         BU[:] = 0.0
@@ -292,3 +329,167 @@ def solve(A, B, p, q, k, l, tol, X0, precond="jacobi", max_cycles=5000, record=F
     if record:
         out["trace"] = trace
     return out
+
+
+def _solve_hard(A, B, p, q, k, l, tol, X0, precond, max_cycles, record):
+    """TRPL+K with hard locking (reading R13); the steps of a cycle are those
+    of `solve`, on the active basis, with every orthogonalisation also
+    against the locked block Q."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    if not (1 <= p <= k and k + max(l, 1) + 1 <= q <= n):
+        raise ValueError("need 1 <= p <= k and k + max(l,1) + 1 <= q <= n")
+    Bm = None if B is None else sp.csr_matrix(B)
+    applyB = (lambda x: x.copy()) if Bm is None else (lambda x: Bm @ x)
+    shifted = precond == "jacobi_shifted"
+    Mapply = None if shifted else make_preconditioner(A, precond)
+    normA = norm1(A)
+    cnt = dict(mv_A=0, mv_B=0, prec=0, mv_check=0)
+
+    X, AX, BX, theta, mvA, mvB = initial_rayleigh_ritz(A, applyB, np.asarray(X0, np.float64))
+    cnt["mv_A"] += mvA
+    cnt["mv_B"] += mvB if Bm is not None else 0
+    Q = np.zeros((n, 0))          # locked vectors
+    BQ = np.zeros((n, 0))
+    lam_q = []                    # their Ritz values
+    Xprev = np.zeros((n, 0))
+    history = []
+    trace = []
+    status = NOT_CONVERGED
+    cycle = 0
+    for cycle in range(1, max_cycles + 1):
+        nq = Q.shape[1]
+        qa, ka, pa = q - nq, k - nq, p - nq          # active basis, restart size, wanted
+        rho = theta[0]                                # the target: smallest active pair
+        if shifted:
+            Mapply = shifted_jacobi_preconditioner(A, Bm, rho)
+        U = np.zeros((n, qa))
+        AU = np.zeros((n, qa))
+        BU = np.zeros((n, qa))
+        T = np.zeros((qa, qa))
+        U[:, :ka], AU[:, :ka], BU[:, :ka] = X, AX, BX
+        T[:ka, :ka] = np.diag(theta[:ka])
+        v = Mapply(AX[:, 0] - rho * BX[:, 0])
+        cnt["prec"] += 1
+        nprev = Xprev.shape[1]
+        m = qa - ka - nprev
+        w = ka
+        broke = False
+        for j in range(m):
+            # CGS2 against [Q, U] in the B-inner product
+            g, Bg, beta, beta0, _ = cgs2(v, np.hstack([Q, U[:, :w]]), np.hstack([BQ, BU[:, :w]]), applyB)
+            if Bm is not None:
+                cnt["mv_B"] += 1
+            if beta <= EPS_BREAKDOWN * beta0:
+                broke = True
+                break
+            U[:, w] = g / beta
+            BU[:, w] = Bg / beta
+            z = A @ U[:, w]
+            cnt["mv_A"] += 1
+            AU[:, w] = z
+            T[: w + 1, w] = U[:, : w + 1].T @ z
+            w += 1
+            if j < m - 1:
+                v = Mapply(z - rho * BU[:, w - 1])
+                cnt["prec"] += 1
+        if broke and w == ka and nprev == 0:
+            status = BREAKDOWN
+            break
+        if nprev > 0:
+            QU = np.hstack([Q, U[:, :w]])
+            BQU = np.hstack([BQ, BU[:, :w]])
+            W = Xprev.copy()
+            for _ in range(2):
+                C = BQU.T @ W
+                W = W - QU @ C
+            w0 = w
+            for c in range(nprev):
+                wv, Bw, beta, _, _ = cgs2(W[:, c], U[:, w0:w], BU[:, w0:w], applyB)
+                if Bm is not None:
+                    cnt["mv_B"] += 1
+                if beta <= EPS_DEPENDENT:
+                    continue
+                U[:, w] = wv / beta
+                BU[:, w] = Bw / beta
+                w += 1
+            for c in range(w0, w):
+                z = A @ U[:, c]
+                cnt["mv_A"] += 1
+                AU[:, c] = z
+                T[: c + 1, c] = U[:, : c + 1].T @ z
+        Xprev_next = X[:, 0: min(l, pa)].copy()
+        theta_all, Y = rayleigh_ritz(T[:w, :w])
+        if record:
+            trace.append(dict(theta=theta_all.copy(), w=w, m=m, nprev=nprev, rho=rho, nq=nq,
+                              QtBU=(BQ.T @ U[:, :w]).copy() if nq else np.zeros((0, w))))
+        Yk = Y[:, :ka]
+        X = U[:, :w] @ Yk
+        AX = AU[:, :w] @ Yk
+        BX = BU[:, :w] @ Yk
+        theta = theta_all[:ka]
+        rn, xn = residual_norms(AX, BX, X, theta)
+        conv = rn <= tol * normA * xn
+        history.append(dict(cycle=cycle, t=nq, rho=rho, nq=nq, theta=theta[:pa].copy(),
+                            resid=(rn / (normA * xn))[:pa].copy(), mv_A=cnt["mv_A"]))
+        # lock the leading run of converged active pairs (R13)
+        s = 0
+        while s < pa and conv[s]:
+            s += 1
+        if s > 0:
+            Q = np.hstack([Q, X[:, :s]])
+            BQ = np.hstack([BQ, BX[:, :s]])
+            lam_q.extend(float(x) for x in theta[:s])
+            X, AX, BX, theta = X[:, s:], AX[:, s:], BX[:, s:], theta[s:]
+            Xprev_next = Xprev_next[:, min(s, Xprev_next.shape[1]):]
+        Xprev = Xprev_next
+        if Q.shape[1] >= p:
+            status = OK
+            break
+    # outputs: locked pairs, then the active ones still wanted, sorted by value
+    nq = Q.shape[1]
+    evecs = np.hstack([Q, X[:, : max(0, p - nq)]])[:, :p]
+    evals = np.concatenate([np.asarray(lam_q), theta[: max(0, p - nq)]])[:p]
+    order = np.argsort(evals, kind="stable")
+    evals, evecs = evals[order], evecs[:, order]
+    AXf = A @ evecs
+    BXf = applyB(evecs) if Bm is None else Bm @ evecs
+    cnt["mv_check"] += p
+    rf = np.linalg.norm(AXf - BXf * evals[None, :], axis=0) / (normA * np.linalg.norm(evecs, axis=0))
+    if status == OK and not np.all(rf <= tol):
+        status = NOT_CONVERGED
+    out = dict(evals=evals, evecs=evecs, resid=rf, status=status, cycles=cycle, normA=normA,
+               history=history, locked=nq, **cnt)
+    if record:
+        out["trace"] = trace
+    return out
+
+
+def lanczos_unrestarted(A, x0, tol, max_mv=5000):
+    """Unrestarted Lanczos for the smallest eigenpair of A (B = I, M = I):
+    the yardstick of the quasi-optimality discussion (Sec. 4; Fig. 1 of
+    Sec. 5.1 compares TRPL+K with it).  The Krylov basis is kept in full and
+    every new vector is re-orthogonalised against all of it by CGS2, so T_j is
+    the exact projection; after each step the smallest Ritz pair of T_j is
+    tested with the residual identity ||A x - theta x|| = beta_{j+1} |y_j|
+    (last component of its eigenvector), against tol ||A||_1.  Returns
+    (theta, matvecs); matvecs counts A x0 as the first."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    normA = norm1(A)
+    Q = np.zeros((n, min(max_mv, n) + 1))
+    q = np.asarray(x0, np.float64)
+    Q[:, 0] = q / np.linalg.norm(q)
+    T = np.zeros((Q.shape[1], Q.shape[1]))
+    theta = None
+    for j in range(min(max_mv, n)):
+        z = A @ Q[:, j]
+        T[: j + 1, j] = Q[:, : j + 1].T @ z
+        T[j, : j + 1] = T[: j + 1, j]
+        w, _, beta, _, _ = cgs2(z, Q[:, : j + 1], Q[:, : j + 1], lambda v: v.copy())
+        th, Y = np.linalg.eigh(T[: j + 1, : j + 1])
+        theta = th[0]
+        if beta * abs(Y[j, 0]) <= tol * normA or beta == 0.0:
+            return float(theta), j + 1
+        Q[:, j + 1] = w / beta
+    return float(theta), min(max_mv, n)

@@ -22,7 +22,9 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "NOT_CONVERGED
                 6: "NOT_SPD_B", 7: "NAN", 8: "ETIMEOUT"}
 F64, F32 = 0, 1
 SMALLEST = 0
-PRECOND_NONE, PRECOND_JACOBI, PRECOND_FSAI, PRECOND_FSAI_LEARNED = 0, 1, 2, 3
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_FSAI, PRECOND_FSAI_LEARNED, PRECOND_JACOBI_SHIFTED = 0, 1, 2, 3, 4
+LOCKING_SOFT, LOCKING_HARD = 0, 1
+ABI_VERSION = 2
 MLP_PARAMS = 5191
 PRECISION_FP64, PRECISION_MIXED = 0, 1
 
@@ -36,7 +38,7 @@ class trplk_params(C.Structure):
     _fields_ = [("p", C.c_int), ("q", C.c_int), ("k", C.c_int), ("l", C.c_int), ("tol", C.c_double),
                 ("max_cycles", C.c_int), ("seed", C.c_uint64), ("which", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("outputs_on_device", C.c_int), ("mlp_weights", C.c_void_p),
-                ("grid", C.c_int * 3), ("mlp_bf16", C.c_int), ("mixed_tol", C.c_double)]
+                ("grid", C.c_int * 3), ("mlp_bf16", C.c_int), ("mixed_tol", C.c_double), ("locking", C.c_int)]
 
 
 class trplk_train_params(C.Structure):
@@ -48,7 +50,8 @@ class trplk_train_params(C.Structure):
 class trplk_info(C.Structure):
     _fields_ = [("cycles", C.c_int), ("refine_cycles", C.c_int), ("mv_A", C.c_int64), ("mv_B", C.c_int64),
                 ("prec_apply", C.c_int64), ("mv_check", C.c_int64), ("seconds", C.c_double),
-                ("nconv", C.c_int), ("normA", C.c_double), ("max_resid", C.c_double), ("launches", C.c_int64)]
+                ("nconv", C.c_int), ("normA", C.c_double), ("max_resid", C.c_double), ("launches", C.c_int64),
+                ("locked", C.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -101,7 +104,7 @@ def _load():
 
 
 LIB = _load()
-if LIB.trplk_abi_version() != 1:
+if LIB.trplk_abi_version() != ABI_VERSION:
     raise ImportError("libtrplk ABI version mismatch")
 
 
@@ -327,16 +330,16 @@ def profile_summary(h):
 # ---------------------------------------------------------------- convenience
 def make_params(p, q, k, l, tol=1e-8, max_cycles=5000, seed=0, precond=PRECOND_JACOBI,
                 precision=PRECISION_FP64, outputs_on_device=0, mixed_tol=0.0, mlp_weights=None, grid=(0, 0, 0),
-                mlp_bf16=1):
+                mlp_bf16=1, locking=LOCKING_SOFT):
     prm = trplk_params(p, q, k, l, tol, max_cycles, seed, SMALLEST, precond, precision, outputs_on_device,
-                       ptr(mlp_weights), (C.c_int * 3)(*grid), int(mlp_bf16), mixed_tol)
+                       ptr(mlp_weights), (C.c_int * 3)(*grid), int(mlp_bf16), mixed_tol, int(locking))
     prm._keep = mlp_weights
     return prm
 
 
 def solve(h: Handle, A: trplk_csr, B=None, *, p, q, k, l, tol=1e-8, X0=None, max_cycles=5000, seed=0,
           precond=PRECOND_JACOBI, precision=PRECISION_FP64, mixed_tol=0.0, mlp_weights=None, grid=(0, 0, 0),
-          mlp_bf16=1):
+          mlp_bf16=1, locking=LOCKING_SOFT):
     """Solve with host outputs (numpy); returns (evals, evecs, resid, status, info dict)."""
     n = A.n
     evals = np.zeros(p)
@@ -344,7 +347,7 @@ def solve(h: Handle, A: trplk_csr, B=None, *, p, q, k, l, tol=1e-8, X0=None, max
     resid = np.zeros(p)
     info = trplk_info()
     params = make_params(p, q, k, l, tol, max_cycles, seed, precond, precision, 0, mixed_tol, mlp_weights, grid,
-                         mlp_bf16)
+                         mlp_bf16, locking)
     X0c = None
     if X0 is not None:
         X0c = X0 if _is_device(X0) else np.ascontiguousarray(np.asarray(X0, np.float64).T)

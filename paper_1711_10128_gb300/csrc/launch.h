@@ -192,6 +192,12 @@ void convert(const Ctx& c, int64_t count, const S* src, D* dst);
 void start_block(const Ctx& c, int64_t n, int64_t ld, int k, uint64_t seed, double* X);
 template <typename S>
 void jacobi_dinv(const Ctx& c, const DevCsr<S>& A, S* dinv);
+// diag[i] = a_ii (FP64)
+void diag_of(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, double* diag);
+// dinv = 1 / max(dA - rho dB, 1e-3 dA) (dB null: 1), rho read from device; rows >= n zero
+template <typename S>
+void shifted_jacobi(const Ctx& c, int64_t n, int64_t ld, const double* dA, const double* dB, const double* rho,
+                    S* dinv);
 // r = x - rho * y   (elementwise, ld rows)
 template <typename S>
 void axpby_shift(const Ctx& c, int64_t ld, const S* x, const S* y, double rho, S* r);

@@ -310,8 +310,9 @@ struct SolveOut {
   int64_t mvA = 0, mvB = 0, prec = 0;
   bool converged = false;
   bool breakdown = false;
-  std::vector<double> theta;   // k Ritz values at exit
+  std::vector<double> theta;   // k Ritz values at exit (locked ones first under hard locking)
   int cur = 0;                 // basis buffer holding X at exit
+  int locked = 0;              // pairs locked (hard locking)
 };
 
 template <typename S>
@@ -328,6 +329,19 @@ struct Solver {
   bool block_refine = false;    // refinement phase: cycles start from all unconverged residuals
   int stall_window = 0;         // >0: stop when the target residual stagnates
   bool stalled = false;
+  // Hard locking: columns [0, nq) of every basis buffer hold the locked Ritz
+  // vectors; T, the Rayleigh-Ritz step and the restart act on the active
+  // columns [nq, ...) while every orthogonalisation also covers the locked
+  // ones.  The active Ritz values sit at theta + toff until the next RR.
+  bool hard_lock = false;
+  int nq = 0, toff = 0;
+  std::vector<double> lam_q;    // locked Ritz values
+  double* theta_out = nullptr;  // [p] final Ritz values in basis-column order
+  // Per-cycle shifted Jacobi M_i = diag(A - rho_i B)^-1: FP64 diagonals of
+  // A and B (B null: identity); the solver rewrites dinv at every cycle
+  const double* diagA = nullptr;
+  const double* diagB = nullptr;
+  S* dinv_var = nullptr;
   double* tmp64 = nullptr;
   const Operator& Aop;
   const Operator& Bop;
@@ -383,6 +397,7 @@ struct Solver {
     rtmp = static_cast<S*>(h->get(tag + ".rtmp", ld * sizeof(S), fresh));
     ttmp = static_cast<S*>(h->get(tag + ".ttmp", ld * sizeof(S), fresh));
     xn = static_cast<double*>(h->get(tag + ".xn", kMaxQ * sizeof(double)));
+    theta_out = static_cast<double*>(h->get(tag + ".theta_out", kMaxQ * sizeof(double)));
   }
 
   S* col(S* M, int j) { return M + (size_t)j * ld; }
@@ -407,13 +422,15 @@ struct Solver {
     }
   }
 
-  // v = M (A x_i - theta_i B x_i) from the stored images (Algorithm 1, restart)
+  // v = M (A x_i - theta_i B x_i) from the stored images (Algorithm 1,
+  // restart); i counts active pairs (column nq + i, Ritz value theta[toff + i])
   void precond_residual(int cur, int i) {
+    const int c0 = nq + i;
     if (MG) {
-      restart_vector<S>(c, ld, col(AU[cur], i), col(BU[cur], i), theta + i, nullptr, PM_IDENTITY, rtmp);
+      restart_vector<S>(c, ld, col(AU[cur], c0), col(BU[cur], c0), theta + toff + i, nullptr, PM_IDENTITY, rtmp);
       apply_fsai(rtmp, v);
     } else {
-      restart_vector<S>(c, ld, col(AU[cur], i), col(BU[cur], i), theta + i, dinv, pmode, v);
+      restart_vector<S>(c, ld, col(AU[cur], c0), col(BU[cur], c0), theta + toff + i, dinv, pmode, v);
     }
   }
 
@@ -442,18 +459,58 @@ struct Solver {
 
   // Rayleigh-Ritz on T[0:w,0:w], rotate (U, AU, BU)[cur] into the other
   // buffer, residual norms of the k new Ritz vectors.  Returns the new cur.
+  // Under hard locking all of this acts on the active columns [nq, w).
   int rr_and_restart(int cur, int w) {
-    rayleigh_ritz(c, w, T, ldT, theta, Y);
+    const int wa = w - nq, ka = k - nq;
+    const size_t o = (size_t)nq * ld;
+    rayleigh_ritz(c, wa, T + (size_t)nq * ldT + nq, ldT, theta, Y);
+    toff = 0;
     const int nx = 1 - cur;
-    ts_rotate<S>(c, ld, w, k, U[cur], Y, w, U[nx]);
-    ts_rotate<S>(c, ld, w, k, AU[cur], Y, w, AU[nx]);
-    if (hasB) ts_rotate<S>(c, ld, w, k, BU[cur], Y, w, BU[nx]);
-    ts_resid<S>(c, ld, k, U[nx], AU[nx], hasB ? BU[nx] : nullptr, theta, rn, xn);
+    ts_rotate<S>(c, ld, wa, ka, U[cur] + o, Y, wa, U[nx] + o);
+    ts_rotate<S>(c, ld, wa, ka, AU[cur] + o, Y, wa, AU[nx] + o);
+    if (hasB) ts_rotate<S>(c, ld, wa, ka, BU[cur] + o, Y, wa, BU[nx] + o);
+    ts_resid<S>(c, ld, ka, U[nx] + o, AU[nx] + o, hasB ? BU[nx] + o : nullptr, theta, rn, xn);
     return nx;
   }
 
-  // Algorithm 1.  X0: double n x k (ld) on the device.
+  // Lock the first s active pairs of buffer `cur` (hard locking): they stay
+  // where they are, a copy goes to the same columns of the other buffer (the
+  // next restart writes only the active columns), their values are kept.
+  void lock(int cur, int s, std::vector<double>& th) {
+    const int other = 1 - cur;
+    const size_t bytes = (size_t)s * ld * sizeof(S);
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(col(U[other], nq), col(U[cur], nq), bytes, cudaMemcpyDeviceToDevice, c.stream));
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(col(AU[other], nq), col(AU[cur], nq), bytes, cudaMemcpyDeviceToDevice, c.stream));
+    if (hasB)
+      TRPLK_CUDA_TRY(cudaMemcpyAsync(col(BU[other], nq), col(BU[cur], nq), bytes, cudaMemcpyDeviceToDevice, c.stream));
+    for (int i = 0; i < s; ++i) lam_q.push_back(th[i]);
+    th.erase(th.begin(), th.begin() + s);
+    nq += s;
+    toff += s;
+  }
+
+  // theta_out[0:p] = the p returned Ritz values in the order of the basis
+  // columns 0..p-1 (locked values first under hard locking)
+  void finish_theta(int pp) {
+    if (nq > 0)
+      TRPLK_CUDA_TRY(cudaMemcpyAsync(theta_out, lam_q.data(), std::min(nq, pp) * sizeof(double),
+                                     cudaMemcpyHostToDevice, c.stream));
+    if (pp > nq)
+      TRPLK_CUDA_TRY(cudaMemcpyAsync(theta_out + nq, theta + toff, (pp - nq) * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, c.stream));
+    h->sync();   // lam_q (host) must stay alive until its copy finished
+  }
+
+  // Algorithm 1.  X0: double n x k (ld) on the device.  On return
+  // theta_out[0:p] holds the Ritz values of basis columns 0..p-1 of U[cur].
   SolveOut run(const double* X0) {
+    SolveOut out = run_cycles(X0);
+    out.locked = nq;
+    finish_theta(p);
+    return out;
+  }
+
+  SolveOut run_cycles(const double* X0) {
     SolveOut out;
     int cur = 0;
     h->clear_status();
@@ -495,8 +552,8 @@ struct Solver {
           throw Error(TRPLK_EINVAL, "start block is numerically rank deficient");
 
     auto converged_vec = [&](const std::vector<double>& rr, const std::vector<double>& xx) {
-      std::vector<char> cv(k);
-      for (int i = 0; i < k; ++i) cv[i] = rr[i] <= tol * normA * xx[i];
+      std::vector<char> cv(rr.size());
+      for (size_t i = 0; i < rr.size(); ++i) cv[i] = rr[i] <= tol * normA * xx[i];
       return cv;
     };
     int t = 0;
@@ -522,9 +579,11 @@ struct Solver {
       h->clear_status();
       {
         ProfScope ps(c, PK_OTHER, 0.0);
-        set_diag_block_kernel<<<1, 256, 0, c.stream>>>(T, ldT, k, theta);
+        set_diag_block_kernel<<<1, 256, 0, c.stream>>>(T + (size_t)nq * ldT + nq, ldT, k - nq, theta + toff);
       }
       check_launch("set_diag_block");
+      // per-cycle preconditioner M_i = diag(A - rho_i B)^-1 (Sec. 3)
+      if (dinv_var) shifted_jacobi<S>(c, n, ld, diagA, diagB, theta + toff + t, dinv_var);
       const int nprev = (xp_buf >= 0) ? xp_count : 0;
       // refinement: first the preconditioned residuals of the other
       // unconverged pairs already near tol (relative residual <= kBlockNear
@@ -612,10 +671,11 @@ struct Solver {
         ts_project<S>(c, ld, w, U[cur], col(AU[cur], w - 1), T + (size_t)(w - 1) * ldT);
       }
       // X_prev for the next cycle: x_t .. x_min(t+l-1, p) of this cycle's X
-      const int nxt_start = t, nxt_count = std::max(0, std::min(t + l, p) - t);
+      // (active pairs; their columns start at nq)
+      const int nxt_start = nq + t, nxt_count = std::max(0, std::min(t + l, p - nq) - t);
       const int old = cur;
       cur = rr_and_restart(cur, w);
-      read_back(k, th, r, x, nullptr, 0);
+      read_back(k - nq, th, r, x, nullptr, 0);
       check_flags(h, kFlagBreakdown);
       cvec = converged_vec(r, x);
       const auto& cv = cvec;
@@ -641,6 +701,27 @@ struct Solver {
       xp_buf = old;
       xp_start = nxt_start;
       xp_count = nxt_count;
+      if (hard_lock) {
+        // lock the leading run of converged active pairs; drop as many X_prev
+        // columns (their copies of the locked vectors); the target stays the
+        // smallest active pair
+        int sl = 0;
+        while (sl < p - nq && cv[sl]) ++sl;
+        if (sl > 0) {
+          const int drop = std::min(sl, xp_count);
+          xp_start += drop;
+          xp_count -= drop;
+          lock(cur, sl, th);
+          r.erase(r.begin(), r.begin() + sl);
+          x.erase(x.begin(), x.begin() + sl);
+          cvec.erase(cvec.begin(), cvec.begin() + sl);
+        }
+        if (nq >= p) {
+          out.converged = true;
+          break;
+        }
+        continue;
+      }
       if (cv[t]) {   // Algorithm 1: flag, drop x_1^prev, advance the target
         ++t;
         if (xp_count > 0) { ++xp_start; --xp_count; }
@@ -695,8 +776,10 @@ void validate_params(const trplk_params* P, int64_t n) {
   if (P->q > n) throw Error(TRPLK_EINVAL, "q must be <= n");
   if (!(P->tol > 0.0)) throw Error(TRPLK_EINVAL, "tol must be > 0");
   if (P->max_cycles < 1) throw Error(TRPLK_EINVAL, "max_cycles must be >= 1");
-  if (P->precond < TRPLK_PRECOND_NONE || P->precond > TRPLK_PRECOND_FSAI_LEARNED)
+  if (P->precond < TRPLK_PRECOND_NONE || P->precond > TRPLK_PRECOND_JACOBI_SHIFTED)
     throw Error(TRPLK_EINVAL, "unsupported preconditioner");
+  if (P->locking != TRPLK_LOCKING_SOFT && P->locking != TRPLK_LOCKING_HARD)
+    throw Error(TRPLK_EINVAL, "unknown locking mode");
   if (P->precond == TRPLK_PRECOND_FSAI_LEARNED && !P->mlp_weights)
     throw Error(TRPLK_EINVAL, "learned FSAI needs mlp_weights");
   if (P->precision != TRPLK_PRECISION_FP64 && P->precision != TRPLK_PRECISION_MIXED)
@@ -782,10 +865,22 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
     const bool hasB = B != nullptr;
     const int64_t n = A->n, ld = round_up(n, 256);
     // preconditioner
-    const int pmode = P->precond == TRPLK_PRECOND_JACOBI ? PM_JACOBI : PM_IDENTITY;
+    const bool shifted = P->precond == TRPLK_PRECOND_JACOBI_SHIFTED;
+    const int pmode = (P->precond == TRPLK_PRECOND_JACOBI || shifted) ? PM_JACOBI : PM_IDENTITY;
     double* dinv64 = nullptr;
     float* dinv32 = nullptr;
-    if (pmode == PM_JACOBI) {
+    double* diagA = nullptr;
+    double* diagB = nullptr;
+    if (shifted) {   // M_i rebuilt by every cycle from the diagonals of A and B
+      dinv64 = static_cast<double*>(h->get("dinv64", ld * sizeof(double), true));
+      diagA = static_cast<double*>(h->get("diagA", ld * sizeof(double), true));
+      diag_of(c, n, Aop.d.rowptr, Aop.d.col, Aop.d.val, diagA);
+      if (hasB) {
+        diagB = static_cast<double*>(h->get("diagB", ld * sizeof(double), true));
+        diag_of(c, n, Bop.d.rowptr, Bop.d.col, Bop.d.val, diagB);
+      }
+      if (mixed) dinv32 = static_cast<float*>(h->get("dinv32", ld * sizeof(float), true));
+    } else if (pmode == PM_JACOBI) {
       dinv64 = static_cast<double*>(h->get("dinv64", ld * sizeof(double), true));
       jacobi_dinv<double>(c, Aop.d, dinv64);
       if (mixed) {
@@ -793,6 +888,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
         convert<float, double>(c, ld, dinv64, dinv32);
       }
     }
+    const bool hard = P->locking == TRPLK_LOCKING_HARD;
     FsaiPrecond fsai;
     if (P->precond == TRPLK_PRECOND_FSAI || P->precond == TRPLK_PRECOND_FSAI_LEARNED)
       fsai = build_fsai_precond(h, Aop.d, P->precond == TRPLK_PRECOND_FSAI ? 0 : 1, P->grid, P->mlp_weights,
@@ -815,13 +911,16 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
     if (!mixed) {
       Solver<double> S(h, "f64", n, P->p, P->q, P->k, P->l, P->tol, P->max_cycles, Aop, Bop, hasB, dinv64, pmode);
       if (fsai.ok) { S.MG = &fsai.G; S.MGT = &fsai.GT; }
+      S.hard_lock = hard;
+      if (shifted) { S.diagA = diagA; S.diagB = diagB; S.dinv_var = dinv64; }
       res = S.run(X0d);
       inf.cycles = res.cycles;
       inf.mv_A = res.mvA;
       inf.mv_B = res.mvB;
       inf.prec_apply = res.prec;
+      inf.locked = res.locked;
       Xfinal = S.U[res.cur];
-      theta_dev = S.theta;
+      theta_dev = S.theta_out;
       breakdown = res.breakdown && !res.converged;
     } else {
       // FP32 phase: to mixed_tol, by default max(tol, 3e-8) -- about half the
@@ -833,7 +932,10 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
                         dinv32, pmode);
       S32.stall_window = 30;
       if (fsai.ok) { S32.MG = &fsai.Gf; S32.MGT = &fsai.GTf; }
+      S32.hard_lock = hard;
+      if (shifted) { S32.diagA = diagA; S32.diagB = diagB; S32.dinv_var = dinv32; }
       SolveOut r32 = S32.run(X0d);
+      inf.locked = r32.locked;
       // promote the k Ritz vectors and refine in FP64 from them
       double* Xr = static_cast<double*>(h->get("Xrefine", (size_t)ld * P->k * sizeof(double)));
       convert<double, float>(c, (int64_t)ld * P->k, S32.U[r32.cur], Xr);
@@ -850,6 +952,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
       S64.check_start = true;
       S64.block_refine = true;
       if (fsai.ok) { S64.MG = &fsai.G; S64.MGT = &fsai.GT; }
+      if (shifted) { S64.diagA = diagA; S64.diagB = diagB; S64.dinv_var = dinv64; }
       SolveOut r64 = S64.run(Xr);
       inf.cycles = r32.cycles;
       inf.refine_cycles = r64.cycles;
@@ -857,7 +960,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
       inf.mv_B = r32.mvB + r64.mvB;
       inf.prec_apply = r32.prec + r64.prec;
       Xfinal = S64.U[r64.cur];
-      theta_dev = S64.theta;
+      theta_dev = S64.theta_out;
       res = r64;
       breakdown = r64.breakdown && !r64.converged;
     }
@@ -871,16 +974,33 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
       inf.nconv += rh[i] <= P->tol;
       inf.max_resid = std::max(inf.max_resid, rh[i]);
     }
-    // outputs
-    const cudaMemcpyKind k2o = P->outputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    TRPLK_CUDA_TRY(cudaMemcpyAsync(evals, theta_dev, P->p * sizeof(double), k2o, c.stream));
-    TRPLK_CUDA_TRY(cudaMemcpy2DAsync(evecs, n * sizeof(double), Xfinal, ld * sizeof(double), n * sizeof(double), P->p,
-                                     k2o, c.stream));
-    if (P->outputs_on_device) {
-      TRPLK_CUDA_TRY(cudaMemcpyAsync(resid, rh.data(), P->p * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-    } else {
-      memcpy(resid, rh.data(), P->p * sizeof(double));
+    // outputs, ascending (hard locking can return the locked pairs out of
+    // order): evals and resid permuted on the host, evecs column by column
+    std::vector<double> thf(P->p);
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(thf.data(), theta_dev, P->p * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    h->sync();
+    std::vector<int> ord(P->p);
+    for (int i = 0; i < P->p; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return thf[a] < thf[b]; });
+    std::vector<double> evs(P->p), rs(P->p);
+    for (int i = 0; i < P->p; ++i) {
+      evs[i] = thf[ord[i]];
+      rs[i] = rh[ord[i]];
     }
+    const cudaMemcpyKind k2o = P->outputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const cudaMemcpyKind h2o = P->outputs_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(evals, evs.data(), P->p * sizeof(double), h2o, c.stream));
+    bool identity = true;
+    for (int i = 0; i < P->p; ++i) identity = identity && ord[i] == i;
+    if (identity) {
+      TRPLK_CUDA_TRY(cudaMemcpy2DAsync(evecs, n * sizeof(double), Xfinal, ld * sizeof(double), n * sizeof(double),
+                                       P->p, k2o, c.stream));
+    } else {
+      for (int i = 0; i < P->p; ++i)
+        TRPLK_CUDA_TRY(cudaMemcpyAsync(evecs + (size_t)i * n, Xfinal + (size_t)ord[i] * ld, n * sizeof(double), k2o,
+                                       c.stream));
+    }
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(resid, rs.data(), P->p * sizeof(double), h2o, c.stream));
     h->sync();
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     inf.launches = h->prof.launches - launches0;

@@ -375,6 +375,36 @@ __global__ void jacobi_dinv_kernel(int64_t n, const int64_t* __restrict__ rowptr
   }
 }
 
+// diag[i] = a_ii (0 where the row has no diagonal entry)
+__global__ void diag_of_kernel(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                               const double* __restrict__ val, double* __restrict__ diag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+      if (col[e] == i) d = val[e];
+    diag[i] = d;
+  }
+}
+
+// The per-cycle shifted Jacobi preconditioner (Sec. 3: M may change every
+// cycle to approximate (A - rho_i B)^-1): dinv_j = 1 / max(a_jj - rho b_jj,
+// 1e-3 a_jj), b_jj = 1 without B; formed in FP64, stored in S; rows >= n 0.
+template <typename S>
+__global__ void shifted_jacobi_kernel(int64_t n, int64_t ld, const double* __restrict__ dA,
+                                      const double* __restrict__ dB, const double* __restrict__ rho_p,
+                                      S* __restrict__ dinv) {
+  const double rho = *rho_p;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ld; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (i < n) {
+      const double a = dA[i];
+      const double d = fmax(a - rho * (dB ? dB[i] : 1.0), 1e-3 * a);
+      v = 1.0 / d;
+    }
+    dinv[i] = (S)v;
+  }
+}
+
 __global__ void sell_lengths_kernel(int64_t m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ perm,
                                     int32_t* __restrict__ lens) {
   const int64_t slice = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -561,6 +591,24 @@ void axpby_shift(const Ctx& c, int64_t ld, const S* x, const S* y, double rho, S
   axpby_shift_kernel<S><<<grid_for(c, ld), 256, 0, c.stream>>>(ld, x, y, rho, r);
   check_launch("axpby_shift");
 }
+
+void diag_of(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, double* diag) {
+  ProfScope ps(c, PK_OTHER, 0.0);
+  diag_of_kernel<<<grid_for(c, n), 256, 0, c.stream>>>(n, rowptr, col, val, diag);
+  check_launch("diag_of");
+}
+
+template <typename S>
+void shifted_jacobi(const Ctx& c, int64_t n, int64_t ld, const double* dA, const double* dB, const double* rho,
+                    S* dinv) {
+  ProfScope ps(c, PK_OTHER, 0.0);
+  shifted_jacobi_kernel<S><<<grid_for(c, ld), 256, 0, c.stream>>>(n, ld, dA, dB, rho, dinv);
+  check_launch("shifted_jacobi");
+}
+template void shifted_jacobi<double>(const Ctx&, int64_t, int64_t, const double*, const double*, const double*,
+                                     double*);
+template void shifted_jacobi<float>(const Ctx&, int64_t, int64_t, const double*, const double*, const double*,
+                                    float*);
 
 void sell_lengths(const Ctx& c, int64_t m, const int64_t* rowptr, const int32_t* perm, int32_t* lens) {
   const int64_t nslices = (m + 31) / 32;

@@ -47,7 +47,7 @@ def test_binding_structs_match_header(binding):
         nfields = sum(len(d.split(",")) for d in decls)
         assert nfields == len(getattr(binding, pyname)._fields_), struct
     assert ctypes.sizeof(binding.trplk_csr) == 48
-    assert binding.LIB.trplk_abi_version() == 1
+    assert binding.LIB.trplk_abi_version() == binding.ABI_VERSION == 2
 
 
 def test_create_without_gpu_fails_cleanly(binding):

@@ -820,3 +820,71 @@ def test_full_size_closed_forms(lib, h, precision):
           "rounding floor", floor)
     assert np.all(err <= r2 / gap + floor)
     assert np.all(err <= 1e-10 * lam)
+
+
+# ---------------------------------------------------------------- hard locking and M(rho_i)
+@pytest.mark.parametrize("case", ["lap2d", "pencil"])
+def test_hard_locking_matches_oracle(lib, h, case):
+    """Hard locking (locked vectors at the front of the basis, T and the
+    Rayleigh-Ritz step on the active columns) against the oracle's hard
+    locking: the FP64 path follows its arithmetic, so cycles, matvecs and the
+    number of locked pairs agree exactly and the eigenvalues to 1e-10; the
+    vectors come back ascending and B-orthonormal."""
+    if case == "lap2d":
+        A, B = W.laplacian_2d(30), None
+        p, q, k, l = 5, 16, 7, 1
+    else:
+        A, B = W.fem_q1_pencil(6, np.random.default_rng(3).uniform(1, 10, (6, 6, 6)))
+        p, q, k, l = 4, 16, 6, 2
+    As = A.to_scipy()
+    Bs = None if B is None else B.to_scipy()
+    X0 = W.start_block(A.n, k, 1)
+    ref = O.solve(As, Bs, p, q, k, l, 1e-10, X0, "jacobi", locking="hard")
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), None if B is None else dev_csr(lib, B), p=p, q=q, k=k,
+                                     l=l, tol=1e-10, X0=X0, locking=lib.LOCKING_HARD)
+    assert rc == lib.OK and ref["status"] == O.OK
+    assert info["cycles"] == ref["cycles"] and info["mv_A"] == ref["mv_A"] and info["locked"] == ref["locked"] == p
+    assert np.all(np.abs(ev - ref["evals"]) <= 1e-10 * np.abs(ref["evals"]))
+    assert np.all(np.diff(ev) >= 0) and np.all(res <= 1e-10)
+    G = X.T @ (X if Bs is None else Bs @ X)
+    assert np.allclose(G, np.eye(p), atol=1e-10)
+
+
+def test_hard_locking_mixed_path(lib, h):
+    """The mixed path locks in its FP32 phase and polishes all p pairs in
+    FP64: same eigenvalues as the oracle's hard-locking run within the
+    Kato-Temple bound of both runs' residuals (another trajectory)."""
+    A = W.diffusion_3d(14, W.lognormal_field(14, 1.0, 2))
+    As = A.to_scipy()
+    p, q, k, l = 6, 20, 8, 1
+    X0 = W.start_block(A.n, k, 3)
+    ref = O.solve(As, None, p, q, k, l, 1e-10, X0, "jacobi", locking="hard")
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), None, p=p, q=q, k=k, l=l, tol=1e-10, X0=X0,
+                                     precision=lib.PRECISION_MIXED, locking=lib.LOCKING_HARD)
+    assert rc == lib.OK and info["locked"] >= 1
+    nA = O.norm1(As)
+    refev = ref["evals"]
+    gap = np.array([np.min(np.abs(np.delete(refev, i) - refev[i])) for i in range(p)])
+    bound = ((res * nA) ** 2 + (ref["resid"] * nA) ** 2) / gap + 1e-10 * np.abs(refev)
+    assert np.all(np.abs(ev - refev) <= bound)
+    assert np.all(np.abs(ev - refev) <= 1e-10 * np.abs(refev))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_shifted_jacobi_matches_oracle(lib, h, precision):
+    """The per-cycle preconditioner M_i = diag(A - rho_i B)^-1 (floored at
+    1e-3 a_jj), rebuilt on the device every cycle from that cycle's shift:
+    FP64 follows the oracle's cycles exactly and its eigenvalues to 1e-10;
+    the mixed path reaches the same eigenvalues."""
+    A = W.diffusion_3d(12, W.lognormal_field(12, 1.0, 5))
+    As = A.to_scipy()
+    p, q, k, l = 5, 18, 7, 1
+    X0 = W.start_block(A.n, k, 2)
+    ref = O.solve(As, None, p, q, k, l, 1e-10, X0, "jacobi_shifted")
+    prec = lib.PRECISION_FP64 if precision == "fp64" else lib.PRECISION_MIXED
+    ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), None, p=p, q=q, k=k, l=l, tol=1e-10, X0=X0,
+                                     precond=lib.PRECOND_JACOBI_SHIFTED, precision=prec)
+    assert rc == lib.OK and ref["status"] == O.OK
+    assert np.all(np.abs(ev - ref["evals"]) <= 1e-10 * np.abs(ref["evals"]))
+    if precision == "fp64":
+        assert info["cycles"] == ref["cycles"] and info["mv_A"] == ref["mv_A"]

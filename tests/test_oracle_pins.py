@@ -350,3 +350,114 @@ def test_breakdown_on_an_invariant_krylov_space_still_gives_exact_eigenpairs():
     assert abs(r["evals"][0] - 1.0) <= 1e-12
     x = r["evecs"][:, 0]
     assert np.linalg.norm(A @ x - x) <= 1e-10
+
+
+# ---------------------------------------------------------------- hard locking (R13), M(rho_i) (R14)
+@pytest.mark.parametrize("precond", ["jacobi", "jacobi_shifted"])
+def test_hard_locking_closed_form_accounting_and_locked_orthogonality(precond):
+    """Hard locking (R13) on the 2D Laplacian: the locked and returned pairs
+    meet the closed form within Krylov-Weinstein (|theta - lambda| <= ||r||),
+    the locked vectors stay B-orthogonal to every active basis they sit beside
+    (Q^T B U = 0 in each cycle), the output is orthonormal, and every cycle
+    still costs q - p_hat matvecs (Tables 2-5's accounting)."""
+    N, p, q, k, l = 24, 5, 16, 7, 1
+    A = W.laplacian_2d(N)
+    As = A.to_scipy()
+    r = O.solve(As, None, p, q, k, l, 1e-10, W.start_block(A.n, k, 1), precond, record=True, locking="hard")
+    assert r["status"] == O.OK and r["locked"] == p
+    lam = lap2d_eigs(N, 2 * p + 2)
+    rabs = r["resid"] * r["normA"]
+    assert np.all(np.diff(r["evals"]) >= 0)
+    for i in range(p):
+        assert np.min(np.abs(lam - r["evals"][i])) <= rabs[i] + 1e-15
+        assert abs(r["evals"][i] - lam[i]) <= 1e-9 * lam[i]
+    X = r["evecs"]
+    assert np.allclose(X.T @ X, np.eye(p), atol=1e-10)
+    assert r["mv_A"] == k + (q - k) * r["cycles"]
+    assert any(tr["nq"] > 0 for tr in r["trace"])
+    for tr in r["trace"]:
+        if tr["nq"]:
+            assert np.abs(tr["QtBU"]).max() <= 1e-12
+
+
+def test_hard_locking_generalized_pencil_brute_force():
+    """Hard locking on the Q1 stiffness/mass pencil against a dense
+    generalized eigensolve (B-inner products throughout, R3 + R13)."""
+    N = 5
+    A, B = W.fem_q1_pencil(N, np.random.default_rng(3).uniform(1, 10, (N, N, N)))
+    As, Bs = A.to_scipy(), B.to_scipy()
+    p, q, k, l = 4, 16, 6, 1
+    r = O.solve(As, Bs, p, q, k, l, 1e-10, W.start_block(A.n, k, 2), "jacobi", locking="hard")
+    assert r["status"] == O.OK
+    brute = sl.eigh(As.toarray(), Bs.toarray(), eigvals_only=True)[:p]
+    assert np.all(np.abs(r["evals"] - brute) <= 1e-9 * brute)
+    X = r["evecs"]
+    assert np.allclose(X.T @ (Bs @ X), np.eye(p), atol=1e-10)
+
+
+def test_hard_locking_with_one_wanted_pair_is_soft_locking():
+    """With p = 1 nothing is locked before the solve ends, so hard locking
+    must reproduce Algorithm 1's iterates exactly: same cycles, matvecs and
+    Ritz values cycle by cycle."""
+    A = W.diffusion_3d(8, W.lognormal_field(8, 1.0, 2))
+    As = A.to_scipy()
+    X0 = W.start_block(A.n, 4, 5)
+    soft = O.solve(As, None, 1, 12, 4, 1, 1e-10, X0, "jacobi")
+    hard = O.solve(As, None, 1, 12, 4, 1, 1e-10, X0, "jacobi", locking="hard")
+    assert soft["cycles"] == hard["cycles"] and soft["mv_A"] == hard["mv_A"]
+    for hs, hh in zip(soft["history"], hard["history"]):
+        assert np.allclose(hs["theta"][:1], hh["theta"][:1], rtol=1e-13, atol=0)
+    assert np.allclose(soft["evals"], hard["evals"], rtol=1e-13, atol=0)
+
+
+def test_shifted_jacobi_on_a_constant_diagonal_is_the_unpreconditioned_method():
+    """R14 on the 2D Laplacian (constant diagonal 4, B = I): M_i is the scalar
+    1/(4 - rho_i), which does not change the Krylov space, the CGS2 basis or
+    any Ritz value -- the iterates must be those of M = I, cycle by cycle."""
+    A = W.laplacian_2d(20)
+    As = A.to_scipy()
+    X0 = W.start_block(A.n, 6, 7)
+    none = O.solve(As, None, 3, 14, 6, 1, 1e-10, X0, "none")
+    shif = O.solve(As, None, 3, 14, 6, 1, 1e-10, X0, "jacobi_shifted")
+    assert none["cycles"] == shif["cycles"] and none["mv_A"] == shif["mv_A"]
+    for a, b in zip(none["history"], shif["history"]):
+        assert np.allclose(a["theta"], b["theta"], rtol=1e-11, atol=0)
+
+
+def test_shifted_jacobi_preconditioner_definition_and_floor():
+    """M_i = diag(max(a_jj - rho b_jj, 1e-3 a_jj))^-1 (R14), with and without B."""
+    A = sp.diags([2.0, 5.0, 10.0]).tocsr()
+    B = sp.diags([1.0, 2.0, 0.5]).tocsr()
+    v = np.array([1.0, 1.0, 1.0])
+    assert np.allclose(O.shifted_jacobi_preconditioner(A, None, 1.0)(v), [1.0, 1 / 4.0, 1 / 9.0])
+    # rho = 3: a - rho b = (-1, -1, 8.5) -> floored to (2e-3, 5e-3, 8.5)
+    assert np.allclose(O.shifted_jacobi_preconditioner(A, B, 3.0)(v), [500.0, 200.0, 1 / 8.5])
+
+
+# ---------------------------------------------------------------- parameter studies (Sec. 5.2, Figs. 1-3)
+def test_unrestarted_lanczos_closed_form_and_quasi_optimality():
+    """The unrestarted Lanczos yardstick reaches the closed-form smallest
+    eigenvalue of the 2D Laplacian (Kato-Temple at its residual), and TRPL+K
+    with the paper's small basis (q = 18, p_hat = 8, l = 1, no
+    preconditioner) needs no more than 1.5 times its matvecs (Sec. 5.2:
+    close to optimal with a very small basis)."""
+    N = 40
+    A = W.laplacian_2d(N)
+    As = A.to_scipy()
+    x0 = W.start_block(A.n, 8, 12)
+    th, mv = O.lanczos_unrestarted(As, x0[:, 0], 1e-9)
+    lam = lap2d_eigs(N, 2)
+    assert abs(th - lam[0]) <= (1e-9 * O.norm1(As)) ** 2 / (lam[1] - lam[0]) + 1e-14
+    r = O.solve(As, None, 1, 18, 8, 1, 1e-9, x0, "none")
+    assert r["status"] == O.OK
+    assert mv <= r["mv_A"] <= 1.5 * mv
+
+
+def test_one_previous_vector_cuts_matvecs_for_five_pairs():
+    """Fig. 3's trend without a preconditioner, p = 5: l = 1 needs clearly
+    fewer matvecs than l = 0 (TRLan, Sec. 5.2) on the 2D Laplacian."""
+    A = W.laplacian_2d(60)
+    As = A.to_scipy()
+    x0 = W.start_block(A.n, 8, 12)
+    mv = {l: O.solve(As, None, 5, 18, 8, l, 1e-8, x0, "none")["mv_A"] for l in (0, 1)}
+    assert mv[1] < 0.9 * mv[0], mv
