@@ -331,15 +331,17 @@ def train_learned_fsai(lib, h, dev):
     return weights, secs, float(losses[:m].mean()), float(losses[-m:].mean()), m, N
 
 
-PRECONDS = {"jacobi": "PRECOND_JACOBI", "fsai": "PRECOND_FSAI", "fsai_learned": "PRECOND_FSAI_LEARNED"}
+PRECONDS = {"jacobi": "PRECOND_JACOBI", "fsai": "PRECOND_FSAI", "fsai_learned": "PRECOND_FSAI_LEARNED",
+            "ic0": "PRECOND_IC0"}
 LEARNED_VARIANTS = [("learned_mixed", "fsai_learned", 1), ("learned_fp64", "fsai_learned", 0),
                     ("classical_mixed", "fsai", 1), ("classical_fp64", "fsai", 0),
+                    ("ic0_mixed", "ic0", 1), ("ic0_fp64", "ic0", 0),
                     ("jacobi_mixed", "jacobi", 1), ("jacobi_fp64", "jacobi", 0)]
 
 
 def learned_block(lib, h, dev, stream, weights, train_info, nops):
-    """Learned FSAI against Jacobi and classical FSAI, each in the mixed and the
-    plain FP64 path, on `nops` held-out anisotropic 128^3 operators (seeds
+    """Learned FSAI against Jacobi, classical FSAI and IC(0) (the paper's kind
+    of preconditioner, Sec. 5.4), each in the mixed and the plain FP64 path, on `nops` held-out anisotropic 128^3 operators (seeds
     2000...): per variant the mean seconds per solve (CUDA events on the
     handle's stream, inputs in HBM, the preconditioner's set-up inside each
     solve), matvecs and cycles, the largest final residual, and the largest

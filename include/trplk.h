@@ -60,10 +60,15 @@ enum {
   TRPLK_PRECOND_JACOBI = 1,        /* M = diag(A)^-1                          */
   TRPLK_PRECOND_FSAI = 2,          /* M = G^T G, classical FSAI on tril(A)    */
   TRPLK_PRECOND_FSAI_LEARNED = 3,  /* M = G^T G, G predicted by the MLP       */
-  TRPLK_PRECOND_JACOBI_SHIFTED = 4 /* M_i = diag(A - rho_i B)^-1, rebuilt every
+  TRPLK_PRECOND_JACOBI_SHIFTED = 4,/* M_i = diag(A - rho_i B)^-1, rebuilt every
                                       cycle (Sec. 3: M may change per cycle to
                                       approximate (A - rho_i B)^-1); each
                                       diagonal entry floored at 1e-3 a_jj     */
+  TRPLK_PRECOND_IC0 = 5            /* no-fill incomplete Cholesky L L^T ~ A
+                                      (the paper's incomplete factorizations,
+                                      Sec. 5.4-5.5), each triangular solve
+                                      applied by 2 Jacobi sweeps:
+                                      M = P^T P, P ~ L^-1 (SPD)               */
 };
 enum {
   TRPLK_LOCKING_SOFT = 0,  /* Algorithm 1: converged pairs stay in the basis   */
@@ -321,12 +326,22 @@ trplk_status trplk_fsai_mlp_init(float* weights, uint64_t seed);
 /* G's values in the order of A's lower pattern.  kind 0: classical FSAI
  * (row i solves A[P_i, P_i] g = e_i, scaled so (G A G^T)_ii = 1; rows of at
  * most 16 lower entries); kind 1: learned (dims = nx, ny, nz of a 7-point
- * operator, weights = host packed MLP parameters, bf16 = precision).
+ * operator, weights = host packed MLP parameters, bf16 = precision); kind 2:
+ * the IC(0) factor L (L L^T = A on the lower pattern; fixed-point sweeps of
+ * the left-looking recurrence run to convergence on the device).
  * A: device CSR, F64.  g: device double[nnz_lower], or NULL to only return
  * *nnz_lower.  EINVAL for a non-symmetric pattern or long rows, NOT_SPD_B if
  * a principal block is not SPD. */
 trplk_status trplk_fsai_values(trplk_handle* h, const trplk_csr* A, int kind, const int32_t* dims,
                                const float* weights, int bf16, double* g, int64_t* nnz_lower);
+
+/* The IC(0) preconditioner of TRPLK_PRECOND_IC0 applied to x (device, FP64,
+ * length n): y = P^T (P x) where P x takes 2 Jacobi sweeps
+ * x_{t+1} = x_t + D^-1 (x - L x_t) from x_0 = D^-1 x on the factor L given by
+ * its values l on A's lower pattern (from trplk_fsai_values with kind 2;
+ * D = diag(L)), and P^T the same sweeps on L^T.  y must not alias x. */
+trplk_status trplk_ic0_apply(trplk_handle* h, const trplk_csr* A, const double* l, const double* x,
+                             double* y);
 
 /* y = G^T (G x) with G given by its values g on A's lower pattern (device,
  * FP64, length n; y must not alias x). */

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "NOT_CONVERGED
                 6: "NOT_SPD_B", 7: "NAN", 8: "ETIMEOUT"}
 F64, F32 = 0, 1
 SMALLEST = 0
-PRECOND_NONE, PRECOND_JACOBI, PRECOND_FSAI, PRECOND_FSAI_LEARNED, PRECOND_JACOBI_SHIFTED = 0, 1, 2, 3, 4
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_FSAI, PRECOND_FSAI_LEARNED, PRECOND_JACOBI_SHIFTED, PRECOND_IC0 = range(6)
 LOCKING_SOFT, LOCKING_HARD = 0, 1
 ABI_VERSION = 2
 MLP_PARAMS = 5191
@@ -90,6 +90,7 @@ def _load():
         "trplk_fsai_mlp_init": (st, [vp, C.c_uint64]),
         "trplk_fsai_values": (st, [vp, C.POINTER(trplk_csr), i32, vp, vp, i32, vp, C.POINTER(C.c_int64)]),
         "trplk_fsai_apply": (st, [vp, C.POINTER(trplk_csr), vp, vp, vp]),
+        "trplk_ic0_apply": (st, [vp, C.POINTER(trplk_csr), vp, vp, vp]),
         "trplk_fsai_loss_grad": (st, [vp, C.POINTER(trplk_csr), vp, vp, i32, vp, i32, dbl, vp, vp]),
         "trplk_fsai_train": (st, [vp, C.POINTER(trplk_csr), vp, i32, C.POINTER(trplk_train_params), vp, vp]),
         "trplk_profile": (st, [vp, i32]),
@@ -250,6 +251,10 @@ def trplk_fsai_values(h, A, kind, dims=None, weights=None, bf16=0, g=None):
     d = (C.c_int32 * 3)(*dims) if dims is not None else None
     h.check(LIB.trplk_fsai_values(h.h, C.byref(A), kind, d, ptr(weights), int(bf16), ptr(g), C.byref(nnz)))
     return nnz.value
+
+
+def trplk_ic0_apply(h, A, l, x, y):
+    return h.check(LIB.trplk_ic0_apply(h.h, C.byref(A), ptr(l), ptr(x), ptr(y)))
 
 
 def trplk_fsai_apply(h, A, g, x, y):

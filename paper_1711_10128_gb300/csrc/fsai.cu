@@ -373,6 +373,102 @@ __global__ void grad_kaporin_kernel(int64_t n, const int64_t* __restrict__ rpL, 
   }
 }
 
+// ---------------------------------------------------------------- IC(0)
+// The no-fill incomplete Cholesky factor L on the lower pattern of A (the
+// paper preconditions with no-fill incomplete factorizations, Sec. 5.4-5.5).
+// The left-looking recurrence s = a_ij - sum_{k<j} l_ik l_jk, l_ij = s / l_jj,
+// l_ii = sqrt(s) is solved as a fixed point: every sweep recomputes all
+// entries in parallel from the previous sweep's values (so the result does
+// not depend on thread order) until no entry moves; the fixed point is the
+// IC(0) factor, reached exactly after at most the depth of the dependency
+// graph and, for these operators, after a few tens of sweeps.
+
+// starting values l_ij = a_ij / sqrt(a_jj), l_ii = sqrt(a_ii)
+__global__ void ic0_init_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ diag,
+                                const int64_t* __restrict__ rpL, const int32_t* __restrict__ colL,
+                                double* __restrict__ l) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t e = rpL[i]; e < rpL[i + 1]; ++e) {
+      const int32_t j = colL[e];
+      l[e] = j == i ? sqrt(diag[i]) : a_at(rp, col, val, i, j) / sqrt(diag[j]);
+    }
+}
+
+// One fixed-point sweep lnew = F(lold); stats[0] = max |lnew - lold|,
+// stats[1] = max |lnew| (non-negative doubles compare as their bit patterns);
+// strict: a non-positive pivot raises kFlagNotSPD (IC(0) breakdown).
+__global__ void __launch_bounds__(256) ic0_sweep_kernel(int64_t n, const int64_t* __restrict__ rp,
+                                                        const int32_t* __restrict__ col,
+                                                        const double* __restrict__ val,
+                                                        const int64_t* __restrict__ rpL,
+                                                        const int32_t* __restrict__ colL,
+                                                        const double* __restrict__ lold, double* __restrict__ lnew,
+                                                        unsigned long long* stats, int strict, int* status) {
+  double dmax = 0.0, vmax = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r0 = rpL[i];
+    for (int64_t e = r0; e < rpL[i + 1]; ++e) {
+      const int32_t j = colL[e];
+      double s = a_at(rp, col, val, i, j);
+      // sum over k < j of l_ik l_jk: merge row i (entries before e) with row j
+      // (entries before its diagonal, which is the last of the row)
+      int64_t pi = r0, pj = rpL[j];
+      const int64_t ej = rpL[j + 1] - 1;
+      while (pi < e && pj < ej) {
+        const int32_t ci = colL[pi], cj = colL[pj];
+        if (ci == cj) {
+          s -= lold[pi] * lold[pj];
+          ++pi;
+          ++pj;
+        } else if (ci < cj) {
+          ++pi;
+        } else {
+          ++pj;
+        }
+      }
+      double v;
+      if (j < i) {
+        v = s / lold[ej];
+      } else {
+        if (!(s > 0.0)) {
+          if (strict) atomicOr(status, kFlagNotSPD);
+          s = 1e-300;
+        }
+        v = sqrt(s);
+      }
+      lnew[e] = v;
+      dmax = fmax(dmax, fabs(v - lold[e]));
+      vmax = fmax(vmax, fabs(v));
+    }
+  }
+  __shared__ double red[2][8];
+  for (int off = 16; off > 0; off >>= 1) {
+    dmax = fmax(dmax, __shfl_down_sync(0xffffffffu, dmax, off));
+    vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = dmax;
+    red[1][threadIdx.x >> 5] = vmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      dmax = fmax(dmax, red[0][w]);
+      vmax = fmax(vmax, red[1][w]);
+    }
+    atomicMax(stats, (unsigned long long)__double_as_longlong(dmax));
+    atomicMax(stats + 1, (unsigned long long)__double_as_longlong(vmax));
+  }
+}
+
+// dinv[i] = 1 / l_ii (the diagonal is the last entry of each lower row)
+__global__ void lower_diag_inv_kernel(int64_t n, const int64_t* __restrict__ rpL, const double* __restrict__ l,
+                                      double* __restrict__ dinv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dinv[i] = 1.0 / l[rpL[i + 1] - 1];
+}
+
 // ---------------------------------------------------------------- MLP backward
 // One tile = 64 rows: threads 0..63 recompute their row's activations and
 // back-propagate dL/do into shared memory; then all 128 threads accumulate
@@ -747,6 +843,57 @@ LossOut loss_grad(trplk_handle* h, const FsaiOp& op, const int32_t* dims, const 
   return out;
 }
 
+// IC(0) values (lower pattern order) into l: fixed-point sweeps from the
+// starting values until the largest change is <= 4 u max |l| (u = 2^-53),
+// read back every 4 sweeps; a last strict sweep checks every pivot.
+void ic0_values(trplk_handle* h, const FsaiOp& op, double* l) {
+  const Ctx& c = h->ctx;
+  double* l2 = static_cast<double*>(h->get("ic0.l2", op.nnzL * sizeof(double)));
+  auto* stats = static_cast<unsigned long long*>(h->get("ic0.stats", 2 * sizeof(unsigned long long)));
+  h->clear_status();
+  {
+    ProfScope ps(c, PK_OTHER, 0.0);
+    ic0_init_kernel<<<blocks_for(c, op.n), 256, 0, c.stream>>>(op.n, op.rp, op.col, op.val, op.diag, op.rpL,
+                                                               op.colL, l);
+    check_launch("ic0_init");
+  }
+  constexpr int kMaxSweeps = 4000;
+  double* cur = l;
+  double* nxt = l2;
+  bool done = false;
+  for (int sw = 1; sw <= kMaxSweeps && !done; ++sw) {
+    const bool check = (sw % 4) == 0 || sw == kMaxSweeps;
+    if (check) TRPLK_CUDA_TRY(cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned long long), c.stream));
+    {
+      ProfScope ps(c, PK_OTHER, 0.0);
+      ic0_sweep_kernel<<<blocks_for(c, op.n), 256, 0, c.stream>>>(op.n, op.rp, op.col, op.val, op.rpL, op.colL, cur,
+                                                                  nxt, stats, 0, c.status);
+      check_launch("ic0_sweep");
+    }
+    std::swap(cur, nxt);
+    if (check) {
+      unsigned long long hs[2];
+      TRPLK_CUDA_TRY(cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, c.stream));
+      h->sync();
+      double dmax, vmax;
+      memcpy(&dmax, &hs[0], 8);
+      memcpy(&vmax, &hs[1], 8);
+      if (!(dmax == dmax) || !(vmax == vmax)) throw Error(TRPLK_NAN, "IC(0) sweeps produced NaN");
+      done = dmax <= 4.0 * 1.1102230246251565e-16 * vmax;
+    }
+  }
+  if (!done) throw Error(TRPLK_EINVAL, "IC(0) fixed-point sweeps did not converge");
+  // one more sweep from the converged values, strict about the pivots
+  {
+    ProfScope ps(c, PK_OTHER, 0.0);
+    ic0_sweep_kernel<<<blocks_for(c, op.n), 256, 0, c.stream>>>(op.n, op.rp, op.col, op.val, op.rpL, op.colL, cur, nxt,
+                                                                stats, 1, c.status);
+    check_launch("ic0_sweep");
+  }
+  if (nxt != l) TRPLK_CUDA_TRY(cudaMemcpyAsync(l, nxt, op.nnzL * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  if (h->read_status() & kFlagNotSPD) throw Error(TRPLK_NOT_SPD_B, "IC(0) breakdown: a pivot is not positive");
+}
+
 void upload_weights(trplk_handle* h, const float* host, float* dev) {
   TRPLK_CUDA_TRY(cudaMemcpyAsync(dev, host, kNParams * sizeof(float), cudaMemcpyHostToDevice, h->ctx.stream));
 }
@@ -767,11 +914,28 @@ FsaiPrecond build_fsai_precond(trplk_handle* h, const DevCsr<double>& A, int kin
     P = static_cast<float*>(h->get("precond.mlp", kNParams * sizeof(float)));
     upload_weights(h, weights_host, P);
   }
-  fsai_values(h, op, kind, dims, P, bf16, g, nullptr);
+  if (kind == 2)
+    ic0_values(h, op, g);
+  else
+    fsai_values(h, op, kind, dims, P, bf16, g, nullptr);
   {
     ProfScope ps(c, PK_OTHER, 0.0);
     gather_kernel<<<blocks_for(c, op.nnzU), 256, 0, c.stream>>>(op.nnzU, op.perm, g, gT);
     check_launch("gather");
+  }
+  if (kind == 2) {
+    const int64_t ld = round_up(op.n, 256);
+    pc.ic0 = true;
+    pc.dinv = static_cast<double*>(h->get("precond.dinv", ld * sizeof(double), true));
+    {
+      ProfScope ps(c, PK_OTHER, 0.0);
+      lower_diag_inv_kernel<<<blocks_for(c, op.n), 256, 0, c.stream>>>(op.n, op.rpL, g, pc.dinv);
+      check_launch("lower_diag_inv");
+    }
+    if (need32) {
+      pc.dinvf = static_cast<float*>(h->get("precond.dinvf", ld * sizeof(float), true));
+      convert<float, double>(c, ld, pc.dinv, pc.dinvf);
+    }
   }
   pc.G = DevCsr<double>{op.n, op.nnzL, op.rpL, op.colL, g};
   pc.GT = DevCsr<double>{op.n, op.nnzU, op.rpU, op.colU, gT};
@@ -829,11 +993,16 @@ trplk_status trplk_fsai_mlp_init(float* weights, uint64_t seed) {
 trplk_status trplk_fsai_values(trplk_handle* h, const trplk_csr* A, int kind, const int32_t* dims,
                                const float* weights, int bf16, double* g, int64_t* nnz_lower) {
   return guarded(h, [&]() -> trplk_status {
-    if (kind != 0 && kind != 1) throw Error(TRPLK_EINVAL, "kind must be 0 (classical) or 1 (learned)");
+    if (kind < 0 || kind > 2) throw Error(TRPLK_EINVAL, "kind must be 0 (classical), 1 (learned) or 2 (IC(0))");
     DevCsr<double> a = dev64(A);
     FsaiOp op = build_pattern(h, a.n, a.rowptr, a.col, a.val, "step.fsai");
     if (nnz_lower) *nnz_lower = op.nnzL;
     if (!g) return TRPLK_OK;
+    if (kind == 2) {
+      ic0_values(h, op, g);
+      h->sync();
+      return TRPLK_OK;
+    }
     float* P = nullptr;
     if (kind == 1) {
       if (!weights) throw Error(TRPLK_EINVAL, "learned FSAI needs MLP weights");
@@ -865,6 +1034,42 @@ trplk_status trplk_fsai_apply(trplk_handle* h, const trplk_csr* A, const double*
     attach_sell(h, GT, "step.fsai.GT", nullptr);
     spmv<double>(c, G, x, t);
     spmv<double>(c, GT, t, y);
+    h->sync();
+    return TRPLK_OK;
+  });
+}
+
+trplk_status trplk_ic0_apply(trplk_handle* h, const trplk_csr* A, const double* l, const double* x, double* y) {
+  return guarded(h, [&]() -> trplk_status {
+    if (!l || !x || !y || x == y) throw Error(TRPLK_EINVAL, "bad IC(0) apply arguments");
+    DevCsr<double> a = dev64(A);
+    const Ctx& c = h->ctx;
+    FsaiOp op = build_pattern(h, a.n, a.rowptr, a.col, a.val, "step.fsai");
+    const int64_t ld = round_up(op.n, 256);
+    double* lT = static_cast<double*>(h->get("step.fsai.gT", op.nnzU * sizeof(double)));
+    double* dv = static_cast<double*>(h->get("step.ic0.dinv", ld * sizeof(double), true));
+    double* in = static_cast<double*>(h->get("step.ic0.in", ld * sizeof(double), true));
+    double* out = static_cast<double*>(h->get("step.ic0.out", ld * sizeof(double), true));
+    double* t[3];
+    for (int i = 0; i < 3; ++i)
+      t[i] = static_cast<double*>(h->get("step.ic0.t" + std::to_string(i), ld * sizeof(double), true));
+    {
+      ProfScope ps(c, PK_OTHER, 0.0);
+      gather_kernel<<<blocks_for(c, op.nnzU), 256, 0, c.stream>>>(op.nnzU, op.perm, l, lT);
+      check_launch("gather");
+    }
+    {
+      ProfScope ps(c, PK_OTHER, 0.0);
+      lower_diag_inv_kernel<<<blocks_for(c, op.n), 256, 0, c.stream>>>(op.n, op.rpL, l, dv);
+      check_launch("lower_diag_inv");
+    }
+    DevCsr<double> L{op.n, op.nnzL, op.rpL, op.colL, l};
+    DevCsr<double> LT{op.n, op.nnzU, op.rpU, op.colU, lT};
+    attach_sell(h, L, "step.ic0.L", nullptr);
+    attach_sell(h, LT, "step.ic0.LT", nullptr);
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(in, x, op.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    ic0_apply<double>(c, ld, L, LT, dv, kIc0Sweeps, in, out, t[0], t[1], t[2]);
+    TRPLK_CUDA_TRY(cudaMemcpyAsync(y, out, op.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
     h->sync();
     return TRPLK_OK;
   });

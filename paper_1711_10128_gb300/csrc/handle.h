@@ -87,12 +87,18 @@ trplk_status guarded(trplk_handle* h, F&& f) {
   }
 }
 
-// FSAI preconditioner M = G^T G for trplk_solve (fsai.cu): kind 0 classical,
-// 1 learned (MLP weights on the host, 7-point grid dims).
+// Preconditioner on A's lower pattern for trplk_solve (fsai.cu): kind 0
+// classical FSAI, 1 learned FSAI (MLP weights on the host, 7-point grid
+// dims), both M = G^T G; kind 2 IC(0), M = P_s^T P_s (ic0_apply).
 struct FsaiPrecond {
   DevCsr<double> G, GT;
   DevCsr<float> Gf, GTf;
   bool ok = false;
+  // kind 2: the IC(0) factor L (in G, L^T in GT), applied by Jacobi sweeps
+  // with the reciprocal of its diagonal
+  bool ic0 = false;
+  double* dinv = nullptr;
+  float* dinvf = nullptr;
 };
 FsaiPrecond build_fsai_precond(trplk_handle* h, const DevCsr<double>& A, int kind, const int32_t* dims,
                                const float* weights_host, bool bf16, bool need32);

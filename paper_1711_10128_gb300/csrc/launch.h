@@ -192,6 +192,13 @@ void convert(const Ctx& c, int64_t count, const S* src, D* dst);
 void start_block(const Ctx& c, int64_t n, int64_t ld, int k, uint64_t seed, double* X);
 template <typename S>
 void jacobi_dinv(const Ctx& c, const DevCsr<S>& A, S* dinv);
+// IC(0) preconditioner out = P_s^T (P_s in): `sweeps` Jacobi sweeps with the
+// factor L (diagonal included; dinv = 1 / diag(L)), then with LT = L^T;
+// t0, t1, t2 scratch vectors (ld rows); out distinct from in and the scratch
+template <typename S>
+void ic0_apply(const Ctx& c, int64_t ld, const DevCsr<S>& L, const DevCsr<S>& LT, const S* dinv, int sweeps,
+               const S* in, S* out, S* t0, S* t1, S* t2);
+constexpr int kIc0Sweeps = 2;   // Jacobi sweeps per triangular solve of the IC(0) preconditioner
 // diag[i] = a_ii (FP64)
 void diag_of(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, double* diag);
 // dinv = 1 / max(dA - rho dB, 1e-3 dA) (dB null: 1), rho read from device; rows >= n zero

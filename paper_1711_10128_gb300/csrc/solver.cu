@@ -349,8 +349,10 @@ struct Solver {
   const DevCsr<S>* B;
   const S* dinv;
   int pmode;
-  const DevCsr<S>* MG = nullptr;    // FSAI factor G (M = G^T G) when set
+  const DevCsr<S>* MG = nullptr;    // FSAI factor G (M = G^T G) when set; IC(0) factor L when ic0_dinv is set
   const DevCsr<S>* MGT = nullptr;
+  const S* ic0_dinv = nullptr;      // IC(0): 1 / diag(L); M = P_s^T P_s by Jacobi sweeps
+  S* itmp[2] = {nullptr, nullptr};
   S* rtmp = nullptr;
   S* ttmp = nullptr;
   double normA;
@@ -402,8 +404,17 @@ struct Solver {
 
   S* col(S* M, int j) { return M + (size_t)j * ld; }
 
-  // out = G^T (G in) (FSAI), two sparse matvecs
+  // out = M in: G^T (G in) (FSAI, two sparse matvecs) or P_s^T (P_s in)
+  // (IC(0), Jacobi sweeps with L and L^T)
   void apply_fsai(const S* in, S* out) {
+    if (ic0_dinv) {
+      for (int i = 0; i < 2; ++i)
+        if (!itmp[i])
+          itmp[i] = static_cast<S*>(h->get(std::string(sizeof(S) == 8 ? "f64" : "f32") + ".itmp" + std::to_string(i),
+                                           ld * sizeof(S), true));
+      ic0_apply<S>(c, ld, *MG, *MGT, ic0_dinv, kIc0Sweeps, in, out, ttmp, itmp[0], itmp[1]);
+      return;
+    }
     spmv<S>(c, *MG, in, ttmp);
     spmv<S>(c, *MGT, ttmp, out);
   }
@@ -776,7 +787,7 @@ void validate_params(const trplk_params* P, int64_t n) {
   if (P->q > n) throw Error(TRPLK_EINVAL, "q must be <= n");
   if (!(P->tol > 0.0)) throw Error(TRPLK_EINVAL, "tol must be > 0");
   if (P->max_cycles < 1) throw Error(TRPLK_EINVAL, "max_cycles must be >= 1");
-  if (P->precond < TRPLK_PRECOND_NONE || P->precond > TRPLK_PRECOND_JACOBI_SHIFTED)
+  if (P->precond < TRPLK_PRECOND_NONE || P->precond > TRPLK_PRECOND_IC0)
     throw Error(TRPLK_EINVAL, "unsupported preconditioner");
   if (P->locking != TRPLK_LOCKING_SOFT && P->locking != TRPLK_LOCKING_HARD)
     throw Error(TRPLK_EINVAL, "unknown locking mode");
@@ -890,9 +901,11 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
     }
     const bool hard = P->locking == TRPLK_LOCKING_HARD;
     FsaiPrecond fsai;
-    if (P->precond == TRPLK_PRECOND_FSAI || P->precond == TRPLK_PRECOND_FSAI_LEARNED)
-      fsai = build_fsai_precond(h, Aop.d, P->precond == TRPLK_PRECOND_FSAI ? 0 : 1, P->grid, P->mlp_weights,
-                                P->mlp_bf16 != 0, mixed);
+    if (P->precond == TRPLK_PRECOND_FSAI || P->precond == TRPLK_PRECOND_FSAI_LEARNED ||
+        P->precond == TRPLK_PRECOND_IC0)
+      fsai = build_fsai_precond(h, Aop.d,
+                                P->precond == TRPLK_PRECOND_FSAI ? 0 : P->precond == TRPLK_PRECOND_IC0 ? 2 : 1, P->grid,
+                                P->mlp_weights, P->mlp_bf16 != 0, mixed);
     // start block (double, ld)
     double* X0d = static_cast<double*>(h->get("X0", (size_t)ld * P->k * sizeof(double), X0 != nullptr));
     if (X0) {
@@ -910,7 +923,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
     bool breakdown = false;
     if (!mixed) {
       Solver<double> S(h, "f64", n, P->p, P->q, P->k, P->l, P->tol, P->max_cycles, Aop, Bop, hasB, dinv64, pmode);
-      if (fsai.ok) { S.MG = &fsai.G; S.MGT = &fsai.GT; }
+      if (fsai.ok) { S.MG = &fsai.G; S.MGT = &fsai.GT; S.ic0_dinv = fsai.dinv; }
       S.hard_lock = hard;
       if (shifted) { S.diagA = diagA; S.diagB = diagB; S.dinv_var = dinv64; }
       res = S.run(X0d);
@@ -931,7 +944,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
       Solver<float> S32(h, "f32", n, P->p, P->q, P->k, P->l, std::max(tol32, P->tol), P->max_cycles, Aop, Bop, hasB,
                         dinv32, pmode);
       S32.stall_window = 30;
-      if (fsai.ok) { S32.MG = &fsai.Gf; S32.MGT = &fsai.GTf; }
+      if (fsai.ok) { S32.MG = &fsai.Gf; S32.MGT = &fsai.GTf; S32.ic0_dinv = fsai.dinvf; }
       S32.hard_lock = hard;
       if (shifted) { S32.diagA = diagA; S32.diagB = diagB; S32.dinv_var = dinv32; }
       SolveOut r32 = S32.run(X0d);
@@ -951,7 +964,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
       S64.skip_converged = true;
       S64.check_start = true;
       S64.block_refine = true;
-      if (fsai.ok) { S64.MG = &fsai.G; S64.MGT = &fsai.GT; }
+      if (fsai.ok) { S64.MG = &fsai.G; S64.MGT = &fsai.GT; S64.ic0_dinv = fsai.dinv; }
       if (shifted) { S64.diagA = diagA; S64.diagB = diagB; S64.dinv_var = dinv64; }
       SolveOut r64 = S64.run(Xr);
       inf.cycles = r32.cycles;

@@ -13,10 +13,17 @@
 // CSR, so the whole block is one contiguous range), then each thread forms its
 // row's dot product from shared memory, gathering x through the read-only
 // cache (for the stencil and FEM operators the gathered x lines are reused
-// from L1/L2 by the neighbouring rows).  No warp-shuffle reductions: on this
+// from L1/L2 by the neighbouring rows).  Every matvec kernel is launched as a
+// programmatic dependent of the previous kernel on the stream (it waits for
+// it before touching memory, but its launch overlaps that kernel's tail); it
+// lets its own dependents start only at exit, since a kernel whose CTAs
+// became resident early would hold SM resources this many-CTA grid needs.
+// No warp-shuffle reductions: on this
 // GPU a shuffle-and-add tree in FP64 costs more FP64 instructions than the
 // products themselves.  A block whose rows hold more nonzeros than the
 // shared-memory chunk is processed in chunks.
+#include <utility>
+
 #include "launch.h"
 #include "tallskinny.cuh"
 
@@ -35,6 +42,7 @@ __global__ void __launch_bounds__(kRows) spmv_kernel(int64_t n, const int64_t* _
                                                      S* __restrict__ y, const double* __restrict__ scale,
                                                      S* __restrict__ g, const S* __restrict__ bx,
                                                      S* __restrict__ bg) {
+  grid_dependency_wait();
   constexpr int CH = Chunk<S>::CH;
   extern __shared__ __align__(16) unsigned char sm[];
   S* s_val = reinterpret_cast<S*>(sm);
@@ -153,6 +161,7 @@ __global__ void __launch_bounds__(256) sell_spmv_kernel(
     int64_t n_cta, int64_t n_warp, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const S* __restrict__ val, const S* __restrict__ x, S* __restrict__ y, const double* __restrict__ scale,
     S* __restrict__ g, const S* __restrict__ bx, S* __restrict__ bg) {
+  grid_dependency_wait();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t b = blockIdx.x;
   if (HYB) {
@@ -230,6 +239,7 @@ __global__ void __launch_bounds__(256) dia_spmv_kernel(int64_t n, int64_t ld, in
                                                        S* __restrict__ y, const double* __restrict__ scale,
                                                        S* __restrict__ g, const S* __restrict__ bx,
                                                        S* __restrict__ bg) {
+  grid_dependency_wait();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   S s0 = 0, s1 = 0;
@@ -260,11 +270,11 @@ void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const doubl
     ProfScope ps(c, prof_kind<S>(scaled ? PK_SPMV_SCALED : PK_SPMV), bytes);
     const unsigned gb = (unsigned)((A.n + 255) / 256);
     if (scaled)
-      dia_spmv_kernel<S, true><<<gb, 256, 0, c.stream>>>(A.n, A.dia_ld, A.ndiag, off, A.dia_val, x, y, scale, g, bx,
-                                                         bg);
+      launch_dependent(dia_spmv_kernel<S, true>, dim3(gb), dim3(256), 0, c.stream, A.n, A.dia_ld, A.ndiag, off,
+                       A.dia_val, x, y, scale, g, bx, bg);
     else
-      dia_spmv_kernel<S, false><<<gb, 256, 0, c.stream>>>(A.n, A.dia_ld, A.ndiag, off, A.dia_val, x, y, nullptr,
-                                                          nullptr, nullptr, nullptr);
+      launch_dependent(dia_spmv_kernel<S, false>, dim3(gb), dim3(256), 0, c.stream, A.n, A.dia_ld, A.ndiag, off,
+                       A.dia_val, x, y, (const double*)nullptr, (S*)nullptr, (const S*)nullptr, (S*)nullptr);
     check_launch("dia_spmv_kernel");
     return;
   }
@@ -283,9 +293,9 @@ void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const doubl
     ProfScope ps(c, prof_kind<S>(scaled ? PK_SPMV_SCALED : PK_SPMV), bytes);
     const unsigned gb = (unsigned)(blocks > 0 ? blocks : 1);
 #define TRPLK_SELL(SC, HY)                                                                                  \
-  sell_spmv_kernel<S, SC, HY><<<gb, 256, 0, c.stream>>>(m, nslices, A.sl_ptr, A.sl_col, A.sl_val, A.sl_perm,  \
-                                                        A.long_rows, A.n_long_cta, A.n_long_warp, A.rowptr,  \
-                                                        A.col, A.val, x, y, scale, g, bx, bg)
+  launch_dependent(sell_spmv_kernel<S, SC, HY>, dim3(gb), dim3(256), 0, c.stream, m, nslices, A.sl_ptr,      \
+                   A.sl_col, A.sl_val, A.sl_perm, A.long_rows, A.n_long_cta, A.n_long_warp, A.rowptr, A.col,  \
+                   A.val, x, y, scale, g, bx, bg)
     if (scaled) {
       if (hyb) TRPLK_SELL(true, true); else TRPLK_SELL(true, false);
     } else {
@@ -306,10 +316,12 @@ void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const doubl
   ProfScope ps(c, prof_kind<S>(scaled ? PK_SPMV_SCALED : PK_SPMV), bytes);
   if (scaled) {
     smem_optin<spmv_kernel<S, true>>((int)smem, c.device);
-    spmv_kernel<S, true><<<(unsigned)blocks, kRows, smem, c.stream>>>(A.n, A.rowptr, A.col, A.val, x, y, scale, g, bx, bg);
+    launch_dependent(spmv_kernel<S, true>, dim3((unsigned)blocks), dim3(kRows), smem, c.stream, A.n, A.rowptr, A.col,
+                     A.val, x, y, scale, g, bx, bg);
   } else {
     smem_optin<spmv_kernel<S, false>>((int)smem, c.device);
-    spmv_kernel<S, false><<<(unsigned)blocks, kRows, smem, c.stream>>>(A.n, A.rowptr, A.col, A.val, x, y, nullptr, nullptr, nullptr, nullptr);
+    launch_dependent(spmv_kernel<S, false>, dim3((unsigned)blocks), dim3(kRows), smem, c.stream, A.n, A.rowptr,
+                     A.col, A.val, x, y, (const double*)nullptr, (S*)nullptr, (const S*)nullptr, (S*)nullptr);
   }
   check_launch("spmv_kernel");
 }
@@ -373,6 +385,21 @@ __global__ void jacobi_dinv_kernel(int64_t n, const int64_t* __restrict__ rowptr
     if (!(d != 0)) atomicOr(status, kFlagNaN);
     dinv[i] = d != 0 ? (S)1 / d : (S)0;
   }
+}
+
+// out = d .* x
+template <typename S>
+__global__ void scale_kernel(int64_t ld, const S* __restrict__ d, const S* __restrict__ x, S* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ld; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = d[i] * x[i];
+}
+
+// one Jacobi sweep's update: out = x + d .* (b - t), t = L x
+template <typename S>
+__global__ void sweep_update_kernel(int64_t ld, const S* __restrict__ x, const S* __restrict__ d,
+                                    const S* __restrict__ b, const S* __restrict__ t, S* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ld; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = x[i] + d[i] * (b[i] - t[i]);
 }
 
 // diag[i] = a_ii (0 where the row has no diagonal entry)
@@ -591,6 +618,47 @@ void axpby_shift(const Ctx& c, int64_t ld, const S* x, const S* y, double rho, S
   axpby_shift_kernel<S><<<grid_for(c, ld), 256, 0, c.stream>>>(ld, x, y, rho, r);
   check_launch("axpby_shift");
 }
+
+// IC(0) preconditioner M b = P_s^T (P_s b): P_s b by `sweeps` Jacobi sweeps
+// x <- x + D^-1 (b - L x) from x = D^-1 b (L with its diagonal D: the same
+// iterate as x <- D^-1 (b - L_strict x)), then the same on L^T.
+template <typename S>
+void ic0_apply(const Ctx& c, int64_t ld, const DevCsr<S>& L, const DevCsr<S>& LT, const S* dinv, int sweeps,
+               const S* in, S* out, S* t0, S* t1, S* t2) {
+  auto scale = [&](const S* x, S* o) {
+    ProfScope ps(c, PK_OTHER, 0.0);
+    scale_kernel<S><<<grid_for(c, ld), 256, 0, c.stream>>>(ld, dinv, x, o);
+    check_launch("scale");
+  };
+  auto update = [&](const S* x, const S* b, const S* t, S* o) {
+    ProfScope ps(c, PK_OTHER, 0.0);
+    sweep_update_kernel<S><<<grid_for(c, ld), 256, 0, c.stream>>>(ld, x, dinv, b, t, o);
+    check_launch("sweep_update");
+  };
+  // forward: the result ends in f (t0 or t2)
+  S* f = t0;
+  S* g = t2;
+  scale(in, f);
+  for (int s = 0; s < sweeps; ++s) {
+    spmv<S>(c, L, f, t1);
+    update(f, in, t1, g);
+    std::swap(f, g);
+  }
+  // backward on L^T with right-hand side f; iterates alternate between out
+  // and g, starting where the last one lands in out
+  S* y = (sweeps % 2 == 0) ? out : g;
+  S* z = (sweeps % 2 == 0) ? g : out;
+  scale(f, y);
+  for (int s = 0; s < sweeps; ++s) {
+    spmv<S>(c, LT, y, t1);
+    update(y, f, t1, z);
+    std::swap(y, z);
+  }
+}
+template void ic0_apply<double>(const Ctx&, int64_t, const DevCsr<double>&, const DevCsr<double>&, const double*,
+                                int, const double*, double*, double*, double*, double*);
+template void ic0_apply<float>(const Ctx&, int64_t, const DevCsr<float>&, const DevCsr<float>&, const float*, int,
+                               const float*, float*, float*, float*, float*);
 
 void diag_of(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, double* diag) {
   ProfScope ps(c, PK_OTHER, 0.0);

@@ -198,6 +198,10 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
   constexpr bool TASKS = (KIND == TS_PROJ || KIND == TS_INNER || KIND == TS_UPDPROJ || KIND == TS_RESID);
   constexpr bool TWO = (KIND == TS_INNER || KIND == TS_RESID);
 
+  // launched as a programmatic dependent of the previous kernel on the
+  // stream: wait until it has finished and its writes are visible before any
+  // global access
+  grid_dependency_wait();
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + 8;
@@ -446,6 +450,11 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
     }
   }
 
+  // The tiles are done: the next kernel's CTAs may now be scheduled as ours
+  // exit (only the reductions below remain).  Triggered this late so that
+  // they never hold SM resources while this kernel still streams.
+  grid_dependents_launch();
+
   // ---------------- agree on a timeout, drain, report
   // Tiles older than issued_upto - stages have landed: the producer issued
   // each later tile only after every consumer warp had released the older
@@ -522,11 +531,22 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
         const int o = o0 + u;
         col[u] = o < w ? o : kMaxQ + (o - w);
       }
-      for (int b = lane; b < nb; b += 32) {
-        const double* pb = a.partials + (size_t)b * a.pstride;
+      // the loads of eight CTAs' partials are issued before they are added
+      // (in the same order as one at a time: the sums are unchanged)
+      for (int b0 = lane; b0 < nb; b0 += 32 * 8) {
+        double pv[8][4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (o0 + u < nout) t[u] += pb[col[u]];
+        for (int q = 0; q < 8; ++q) {
+          const int b = b0 + 32 * q;
+          const double* pb = a.partials + (size_t)b * a.pstride;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) pv[q][u] = (b < nb && o0 + u < nout) ? pb[col[u]] : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (b0 + 32 * q < nb) t[u] += pv[q][u];
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)

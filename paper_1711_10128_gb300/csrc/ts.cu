@@ -56,7 +56,7 @@ void launch_kind(const Ctx& c, TSArgs<S>& a, size_t fixed, size_t stage, double 
   int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)c.sms * per_sm);
   grid = std::min(grid, kMaxPartials);
   ProfScope ps(c, prof_kind<S>(PK_TS_PROJ + KIND), bytes);
-  ts_kernel<S, KIND, MAXW><<<grid, Tile<S>::TR + 32, smem, c.stream>>>(a);
+  launch_dependent(ts_kernel<S, KIND, MAXW>, dim3(grid), dim3(Tile<S>::TR + 32), smem, c.stream, a);
   check_launch("ts_kernel");
 }
 

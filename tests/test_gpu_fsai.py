@@ -169,3 +169,51 @@ def test_training_reduces_loss_and_learned_fsai_beats_jacobi(lib, h):
         gains.append(ij["mv_A"] / il["mv_A"])
     print("matvec gain of the learned FSAI over Jacobi on held-out operators:", gains)
     assert min(gains) > 1.0
+
+
+# ---------------------------------------------------------------- IC(0)
+def test_ic0_factor_matches_oracle(lib, h):
+    """The IC(0) factor from the device's fixed-point sweeps (run to
+    convergence) against the oracle's left-looking recurrence, to 1e-12."""
+    from oracle import ic0 as I
+    for A in (aniso(11, 3), W.fem_q1_pencil(6, np.random.default_rng(1).uniform(1, 10, (6, 6, 6)))[0],
+              W.chung_lu_laplacian(3000, 8.0, 2.1, 4)):
+        Lref = I.ic0(A.to_scipy())
+        nnz = lib.trplk_fsai_values(h, dcsr(lib, A), 2)
+        assert nnz == Lref.nnz
+        l = torch.zeros(nnz, dtype=torch.float64, device="cuda")
+        lib.trplk_fsai_values(h, dcsr(lib, A), 2, g=l)
+        assert np.allclose(l.cpu().numpy(), Lref.data, rtol=1e-12, atol=1e-13 * np.abs(Lref.data).max())
+
+
+def test_ic0_apply_matches_oracle(lib, h):
+    """M x = P^T (P x) with two Jacobi sweeps per triangular solve, to 1e-12."""
+    from oracle import ic0 as I
+    A = aniso(10, 8)
+    L = I.ic0(A.to_scipy())
+    x = np.random.default_rng(3).standard_normal(A.n)
+    y = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    lib.trplk_ic0_apply(h, dcsr(lib, A), torch.from_numpy(L.data).cuda(), torch.from_numpy(x).cuda(), y)
+    ref = I.apply_M(L, x, 2)
+    assert np.allclose(y.cpu().numpy(), ref, rtol=1e-12, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ic0_solve_matches_oracle(lib, h, precision):
+    """TRPL+K preconditioned by IC(0): the FP64 path follows the oracle's
+    cycles and its eigenvalues to 1e-10; the mixed path reaches the same
+    eigenvalues."""
+    from oracle import ic0 as I
+    N = 12
+    A = aniso(N, 11)
+    As = A.to_scipy()
+    p, q, k, l = 4, 18, 6, 1
+    X0 = W.start_block(A.n, k, 1)
+    ref = O.solve(As, None, p, q, k, l, 1e-10, X0, I.preconditioner(As, 2))
+    prec = lib.PRECISION_FP64 if precision == "fp64" else lib.PRECISION_MIXED
+    ev, X, res, rc, info = lib.solve(h, dcsr(lib, A), None, p=p, q=q, k=k, l=l, tol=1e-10, X0=X0,
+                                     precond=lib.PRECOND_IC0, precision=prec)
+    assert rc == lib.OK and ref["status"] == O.OK
+    assert np.all(np.abs(ev - ref["evals"]) <= 1e-10 * np.abs(ref["evals"]))
+    if precision == "fp64":
+        assert info["cycles"] == ref["cycles"]
