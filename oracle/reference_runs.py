@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import json
 import os
+import platform
 import sys
 import time
 
@@ -64,7 +65,8 @@ def run(name):
     secs = time.perf_counter() - t0
     return dict(n=A.n, nnz=A.nnz, p=cfg["p"], q=cfg["q"], k=cfg["k"], l=cfg["l"], tol=cfg["tol"],
                 status=r["status"], cycles=r["cycles"], mv_A=r["mv_A"], evals=[float(x) for x in r["evals"]],
-                resid=[float(x) for x in r["resid"]], seconds=secs, cores=os.cpu_count())
+                resid=[float(x) for x in r["resid"]], seconds=secs, cores=os.cpu_count(),
+                host=f"{platform.machine()}, {os.cpu_count()} cores")
 
 
 def main(names):
