@@ -162,9 +162,11 @@ void sell_fill(const Ctx& c, int64_t m, const int64_t* rowptr, const int32_t* co
 // ---- tall-skinny passes (ts.cu).  All vectors have ld rows (zero padded).
 template <typename S>
 void ts_project(const Ctx& c, int64_t ld, int w, const S* BU, const S* v, double* hout);
+// zsrc, bsrc (block TRPL+K): form v = M(zsrc - rho bsrc) instead of M(z - rho bg)
 template <typename S>
 void ts_inner(const Ctx& c, int64_t ld, int w, const S* U, const S* BU, const S* z, const S* bg,
-              const S* dinv, int pmode, double rho, S* v, double* tcol, double* h1);
+              const S* dinv, int pmode, double rho, S* v, double* tcol, double* h1, const S* zsrc = nullptr,
+              const S* bsrc = nullptr);
 template <typename S>
 void ts_update_project(const Ctx& c, int64_t ld, int w, const S* U, const S* BU, const double* h,
                        S* v, double* hout);
@@ -181,6 +183,13 @@ void ts_rotate(const Ctx& c, int64_t ld, int w, int k, const S* U, const double*
 template <typename S>
 void ts_resid(const Ctx& c, int64_t ld, int k, const S* X, const S* AX, const S* BX,
               const double* theta, double* rnorm, double* xnorm);
+
+// ---- restart rotation on the tensor cores (rotate_tc.cu): X = U Y(:, 0:k),
+// FP32 U and X, FP64 Y, w <= 64, k <= 32, ld % 128 == 0
+bool rotate_tc_fits(int w, int k);
+void rotate_tc(const Ctx& c, int64_t ld, int w, int k, const float* U, const double* Y, int ldY, float* X);
+// whether ts_rotate<float> takes the tensor-core path for this shape
+bool rotate_tc_preferred(int w, int k);
 
 // ---- small kernels (misc.cu)
 // v = M (AX[:, t] - theta_t BX[:, t]); pmode PM_* ; theta_t read from device.

@@ -113,6 +113,8 @@ TSArgs<S> blank() {
   a.matsel[0] = 0;
   a.matsel[1] = 0;
   a.matsel[2] = 0;
+  a.vsrc = 0;
+  a.bsrc = 1;
   return a;
 }
 
@@ -130,7 +132,8 @@ void ts_project(const Ctx& c, int64_t ld, int w, const S* BU, const S* v, double
 
 template <typename S>
 void ts_inner(const Ctx& c, int64_t ld, int w, const S* U, const S* BU, const S* z, const S* bg,
-              const S* dinv, int pmode, double rho, S* v, double* tcol, double* h1) {
+              const S* dinv, int pmode, double rho, S* v, double* tcol, double* h1, const S* zsrc,
+              const S* bsrc) {
   TSArgs<S> a = blank<S>();
   a.mat[0] = U;
   if (BU == U) { a.nmat = 1; a.matsel[1] = 0; }
@@ -141,6 +144,14 @@ void ts_inner(const Ctx& c, int64_t ld, int w, const S* U, const S* BU, const S*
     a.vec[1] = bg;
     a.nvec = 2;
     if (pmode == PM_JACOBI) { a.vec[2] = dinv; a.nvec = 3; }
+    if (zsrc) {   // block TRPL+K: the new vector comes from another column
+      if (pmode != PM_JACOBI) a.vec[2] = z;   // placeholder at the Jacobi slot
+      a.vec[3] = zsrc;
+      a.vec[4] = bsrc;
+      a.nvec = 5;
+      a.vsrc = 3;
+      a.bsrc = 4;
+    }
   }
   a.pmode = pmode; a.rho = rho; a.vout = v;
   a.w = w; a.ld = ld; a.out0 = tcol; a.out1 = h1;
@@ -196,6 +207,12 @@ void ts_dot_norm(const Ctx& c, int64_t ld, const S* v, const S* bv, const double
 template <typename S>
 void ts_rotate(const Ctx& c, int64_t ld, int w, int k, const S* U, const double* Y, int ldY, S* X) {
   if (k > kMaxK) throw Error(TRPLK_EINVAL, "rotation width exceeds 32");
+  if constexpr (sizeof(S) == 4) {
+    if (rotate_tc_preferred(w, k)) {
+      rotate_tc(c, ld, w, k, U, Y, ldY, X);
+      return;
+    }
+  }
   TSArgs<S> a = blank<S>();
   a.mat[0] = U; a.nmat = 1;
   a.nvec = 0;
@@ -220,7 +237,7 @@ void ts_resid(const Ctx& c, int64_t ld, int k, const S* X, const S* AX, const S*
 #define TRPLK_INST(S)                                                                                 \
   template void ts_project<S>(const Ctx&, int64_t, int, const S*, const S*, double*);                 \
   template void ts_inner<S>(const Ctx&, int64_t, int, const S*, const S*, const S*, const S*,         \
-                            const S*, int, double, S*, double*, double*);                             \
+                            const S*, int, double, S*, double*, double*, const S*, const S*);         \
   template void ts_update_project<S>(const Ctx&, int64_t, int, const S*, const S*, const double*, S*, \
                                      double*);                                                        \
   template void ts_update_norm<S>(const Ctx&, int64_t, int, const S*, const double*, const double*,   \
