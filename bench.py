@@ -282,6 +282,22 @@ def oracle_sample(A, B, cycles_hint=None):
     return secs, text
 
 
+def oracle_full_runs(key):
+    """Every full oracle solve of a workload stored with its wall time
+    (oracle/reference_runs.json: the stored run and the timings added from
+    other hosts), as {host, seconds, cycles}: the check on the extrapolated
+    CPU baseline."""
+    path = os.path.join(ROOT, "oracle", "reference_runs.json")
+    if not os.path.exists(path):
+        return []
+    d = json.load(open(path)).get(key)
+    if not d:
+        return []
+    runs = [{"host": d.get("host"), "seconds": d.get("seconds"), "cycles": d.get("cycles")}]
+    runs += [{"host": t["host"], "seconds": t["seconds"], "cycles": t["cycles"]} for t in d.get("other_host_timings", [])]
+    return runs
+
+
 def run_reference(args, world, rank, pg):
     if rank != 0:
         return 0
@@ -298,7 +314,8 @@ def run_reference(args, world, rank, pg):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(A, B, "cpu oracle fp64 (jacobi)"),
-            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "full_solves_timed": oracle_full_runs(WORKLOAD["key"])},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -457,19 +474,19 @@ def run_ours(args, world, rank, local, pg):
         grid = (P["N"],) * 3
         setup = train_info
 
-    def params(precision, precond, on_device):
+    def params(precision, precond, on_device, block=1):
         return lib.make_params(P["p"], P["q"], P["k"], P["l"], P["tol"], 5000, P["seed"],
                                getattr(lib, PRECONDS[precond]), precision, on_device, 0.0,
-                               weights if precond == "fsai_learned" else None, grid, 1)
+                               weights if precond == "fsai_learned" else None, grid, 1, block=block)
 
-    def solve_device(precision, precond):
+    def solve_device(precision, precond, block=1):
         info = lib.trplk_info()
-        rc = lib.trplk_solve(h, Ad, Bd, params(precision, precond, 1), None, ev_d, X_d, r_d, info)
+        rc = lib.trplk_solve(h, Ad, Bd, params(precision, precond, 1, block), None, ev_d, X_d, r_d, info)
         return rc, info.as_dict()
 
-    def timed(precision, precond, steps, warmup, profile=False):
+    def timed(precision, precond, steps, warmup, profile=False, block=1):
         for _ in range(warmup):
-            solve_device(precision, precond)
+            solve_device(precision, precond, block)
         torch.cuda.synchronize(dev)
         barrier(pg, local)
         sampler = ClockSampler(local)
@@ -481,7 +498,7 @@ def run_ours(args, world, rank, local, pg):
         infos = []
         e0.record(stream)
         for _ in range(steps):
-            rc, info = solve_device(precision, precond)
+            rc, info = solve_device(precision, precond, block)
             if rc != lib.OK:
                 raise RuntimeError(f"solve did not converge: {info}")
             infos.append(info)
@@ -569,6 +586,18 @@ def run_ours(args, world, rank, local, pg):
         if len(comp) > 1:
             out["comparisons"] = comp
 
+    # block TRPL+K on the same operator (targets per cycle b; b = 1 is the headline)
+    if not args.no_fp64:
+        blk = {}
+        for b in (2, 4):
+            if P["k"] + b + P["l"] > P["q"]:
+                continue
+            ms, inf, _, _ = timed(lib.PRECISION_MIXED, P["precond"], 1, 1, block=b)
+            blk[b] = {"seconds": max_over_ranks(pg, ms, local) / 1e3, "cycles": inf[-1]["cycles"],
+                      "refine_cycles": inf[-1]["refine_cycles"], "mv_A": inf[-1]["mv_A"],
+                      "max_resid": inf[-1]["max_resid"], "eig_err_vs_oracle": eig_error(ev_d.cpu().numpy(), oracle_ref)}
+        out["block_trplk_mixed"] = blk
+
     # end to end: host CSR in pinned memory, host outputs
     if not args.no_e2e:
         def to_host(M):
@@ -605,7 +634,7 @@ def run_ours(args, world, rank, local, pg):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         secs, sample = oracle_sample(A, B, fp64_cycles)
         out["cpu_baseline"] = {"value": secs, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-                               "sample": sample}
+                               "sample": sample, "full_solves_timed": oracle_full_runs(WORKLOAD["key"])}
     h.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -130,7 +130,15 @@ typedef struct {
  *             the restart cover the active columns only; the target is always
  *             the smallest active pair; the solve ends when p pairs are
  *             locked.  The mixed path locks in its FP32 phase; its FP64
- *             refinement polishes all p pairs with soft locking.          */
+ *             refinement polishes all p pairs with soft locking.
+ *  block      block size b of block TRPL+K (0 or 1: Algorithm 1; the paper
+ *             leaves a block TRPL+K to future work, Sec. 5.5).  A cycle
+ *             works on the targets t .. t+b-1: its first b Lanczos vectors
+ *             are their preconditioned residuals, and every later one is
+ *             M(A g - rho_i B g) from the vector g of the same sequence b
+ *             columns back (rho_i = theta_{t+i}), B-orthogonalised by CGS2
+ *             against the whole basis.  Needs b <= k, k + b + l <= q and
+ *             soft locking; the FP64 refinement of the mixed path uses b = 1. */
 typedef struct {
   int p, q, k, l;
   double tol;
@@ -145,6 +153,7 @@ typedef struct {
   int mlp_bf16;
   double mixed_tol;
   int locking;
+  int block;
 } trplk_params;
 
 /* Counters and timings of one solve. */
@@ -248,6 +257,15 @@ trplk_status trplk_rayleigh_ritz(trplk_handle* h, int w, const double* T, int ld
  * with Y double w x k column-major (ldY).  Xout: n x k (ld), must not alias U. */
 trplk_status trplk_rotate(trplk_handle* h, int dtype, int64_t n, int64_t ld, int w, int k,
                           const void* U, const double* Y, int ldY, void* Xout);
+
+/* The same rotation on the tensor cores, FP32 U and Xout (trplk_rotate takes
+ * this path for FP32 data when k >= 24): each 128-row tile of U is one
+ * tcgen05.mma product with Y^T in tensor memory, BF16 operands from an exact
+ * three-way split of every FP32 value (and of Y to FP32 accuracy), the six
+ * products of parts whose order adds up to at most two summed in FP32, so the
+ * result keeps FP32 accuracy.  w <= 64, k <= 32; EINVAL otherwise. */
+trplk_status trplk_rotate_tc(trplk_handle* h, int64_t n, int64_t ld, int w, int k, const float* U,
+                             const double* Y, int ldY, float* Xout);
 
 /* Residual norms from stored images: rnorm[i] = ||AX_i - theta_i BX_i||_2 and
  * xnorm[i] = ||X_i||_2, i < k.  BX == NULL means B = I (BX = X). */

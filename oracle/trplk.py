@@ -60,6 +60,16 @@ R13 Hard locking (locking="hard"; Sec. 3 says it can replace the soft locking
     active pair; locking s pairs drops the first s columns of X_prev.  The
     solve ends when p pairs are locked.  Outputs are sorted by value.  Each
     cycle still costs q - p_hat matvecs, so the accounting of R6 holds.
+R15 Block TRPL+K (block=b; the paper leaves a block TRPL+K to future work,
+    Sec. 5.5): each cycle works on the b targets t .. t+b-1 (capped at
+    p_hat - 1) with shifts rho_i = theta_{t+i}; the cycle's first b Lanczos
+    vectors are M r_{t+i}, and every later one is M(A g - rho_i B g) from the
+    vector g appended b steps earlier (so the columns cycle through the b
+    sequences), each B-orthogonalised by CGS2 against every column already in
+    the basis -- block Gram-Schmidt taken column by column, so the basis
+    after each block spans the block Krylov space.  The target advances as in
+    Algorithm 1 (R9); +K and the restart are unchanged, and each cycle still
+    costs q - p_hat matvecs.  block = 1 is Algorithm 1.
 R14 Per-cycle preconditioner (precond="jacobi_shifted"; Sec. 3 notes that M
     may change every cycle to approximate (A - rho_i B)^-1): the shifted
     Jacobi preconditioner M_i = diag(d)^-1 with
@@ -186,18 +196,21 @@ def residual_norms(AX, BX, X, theta):
     return np.linalg.norm(R, axis=0), np.linalg.norm(X, axis=0)
 
 
-def solve(A, B, p, q, k, l, tol, X0, precond="jacobi", max_cycles=5000, record=False, locking="soft"):
+def solve(A, B, p, q, k, l, tol, X0, precond="jacobi", max_cycles=5000, record=False, locking="soft", block=1):
     """TRPL+K (Algorithm 1) for the p smallest eigenpairs of (A, B).
 
     A, B: scipy CSR (B None means identity); q: maximum basis size; k: thick
     restart size p_hat >= p; l: maximum number of +K vectors; X0: n x k start
     block; precond: "jacobi", "none", "jacobi_shifted" (R14) or a function;
-    locking: "soft" (Algorithm 1) or "hard" (R13).  Returns a dict with
+    locking: "soft" (Algorithm 1) or "hard" (R13); block: the block size of
+    R15 (1: Algorithm 1; soft locking only).  Returns a dict with
     evals, evecs (B-orthonormal), resid (final FP64 check with fresh matvecs,
     relative to ||A||_1 ||x||_2), status, cycles, matvec counters and a
     per-cycle history.
     """
     if locking == "hard":
+        if block != 1:
+            raise ValueError("block TRPL+K is defined with soft locking")
         return _solve_hard(A, B, p, q, k, l, tol, X0, precond, max_cycles, record)
     if locking != "soft":
         raise ValueError(f"unknown locking {locking!r}")
@@ -205,6 +218,8 @@ def solve(A, B, p, q, k, l, tol, X0, precond="jacobi", max_cycles=5000, record=F
     n = A.shape[0]
     if not (1 <= p <= k and k + max(l, 1) + 1 <= q <= n):
         raise ValueError("need 1 <= p <= k and k + max(l,1) + 1 <= q <= n")
+    if not (1 <= block <= k and k + block + l <= q):
+        raise ValueError("need 1 <= block <= k and k + block + l <= q")
     Bm = None if B is None else sp.csr_matrix(B)
     applyB = (lambda x: x.copy()) if Bm is None else (lambda x: Bm @ x)
     shifted = precond == "jacobi_shifted"
@@ -236,15 +251,20 @@ def solve(A, B, p, q, k, l, tol, X0, precond="jacobi", max_cycles=5000, record=F
         T[:] = 0.0
         U[:, :k], AU[:, :k], BU[:, :k] = X, AX, BX
         T[:k, :k] = np.diag(theta[:k])
-        # first Lanczos vector: u = M (A x_t - rho B x_t)   (Algorithm 1, restart)
-        v = Mapply(AX[:, t] - rho * BX[:, t])
-        cnt["prec"] += 1
+        # the cycle's targets and shifts (R15; block = 1: Algorithm 1)
+        tg = [min(t + i, k - 1) for i in range(block)]
+        rhos = [theta[i] for i in tg]
+        # first Lanczos vectors: u_i = M (A x_ti - rho_i B x_ti)   (Algorithm 1, restart)
+        pend = [Mapply(AX[:, i] - theta[i] * BX[:, i]) for i in tg]
+        cnt["prec"] += len(pend)
         nprev = Xprev.shape[1]
         m = q - k - nprev
         w = k
         broke = False
-        # inner preconditioned Lanczos building G and T (eq. (UpdateT))
+        # inner preconditioned Lanczos building G and T (eq. (UpdateT)); with
+        # block > 1 the columns cycle through the b sequences (R15)
         for j in range(m):
+            v = pend.pop(0)
             g, Bg, beta, beta0, _ = cgs2(v, U[:, :w], BU[:, :w], applyB)
             if Bm is not None:
                 cnt["mv_B"] += 1
@@ -258,8 +278,8 @@ def solve(A, B, p, q, k, l, tol, X0, precond="jacobi", max_cycles=5000, record=F
             AU[:, w] = z
             T[: w + 1, w] = U[:, : w + 1].T @ z
             w += 1
-            if j < m - 1:
-                v = Mapply(z - rho * BU[:, w - 1])
+            if j + len(pend) < m - 1:
+                pend.append(Mapply(z - rhos[j % block] * BU[:, w - 1]))
                 cnt["prec"] += 1
         if broke and w == k and nprev == 0:
             status = BREAKDOWN

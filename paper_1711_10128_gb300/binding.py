@@ -38,7 +38,8 @@ class trplk_params(C.Structure):
     _fields_ = [("p", C.c_int), ("q", C.c_int), ("k", C.c_int), ("l", C.c_int), ("tol", C.c_double),
                 ("max_cycles", C.c_int), ("seed", C.c_uint64), ("which", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("outputs_on_device", C.c_int), ("mlp_weights", C.c_void_p),
-                ("grid", C.c_int * 3), ("mlp_bf16", C.c_int), ("mixed_tol", C.c_double), ("locking", C.c_int)]
+                ("grid", C.c_int * 3), ("mlp_bf16", C.c_int), ("mixed_tol", C.c_double), ("locking", C.c_int),
+                ("block", C.c_int)]
 
 
 class trplk_train_params(C.Structure):
@@ -82,6 +83,7 @@ def _load():
         "trplk_rayleigh_ritz": (st, [vp, i32, vp, i32, vp, vp]),
         "trplk_rotate": (st, [vp, i32, i64, i64, i32, i32, vp, vp, i32, vp]),
         "trplk_residual_norms": (st, [vp, i32, i64, i64, i32, vp, vp, vp, vp, vp, vp]),
+        "trplk_rotate_tc": (st, [vp, i64, i64, i32, i32, vp, vp, i32, vp]),
         "trplk_start_block": (st, [vp, i64, i64, i32, C.c_uint64, vp]),
         "trplk_check_residuals": (st, [vp, C.POINTER(trplk_csr), C.POINTER(trplk_csr), i64, i32, vp, vp, dbl, vp]),
         "trplk_project_noalloc": (st, [i32, i64, i64, i32, vp, vp, vp, vp]),
@@ -217,6 +219,10 @@ def trplk_rotate(h, dtype, n, ld, w, k, U, Y, ldY, X):
     return h.check(LIB.trplk_rotate(h.h, dtype, n, ld, w, k, ptr(U), ptr(Y), ldY, ptr(X)))
 
 
+def trplk_rotate_tc(h, n, ld, w, k, U, Y, ldY, X):
+    return h.check(LIB.trplk_rotate_tc(h.h, n, ld, w, k, ptr(U), ptr(Y), ldY, ptr(X)))
+
+
 def trplk_residual_norms(h, dtype, n, ld, k, X, AX, BX, theta, rnorm, xnorm):
     return h.check(LIB.trplk_residual_norms(h.h, dtype, n, ld, k, ptr(X), ptr(AX), ptr(BX), ptr(theta),
                                             ptr(rnorm), ptr(xnorm)))
@@ -335,16 +341,16 @@ def profile_summary(h):
 # ---------------------------------------------------------------- convenience
 def make_params(p, q, k, l, tol=1e-8, max_cycles=5000, seed=0, precond=PRECOND_JACOBI,
                 precision=PRECISION_FP64, outputs_on_device=0, mixed_tol=0.0, mlp_weights=None, grid=(0, 0, 0),
-                mlp_bf16=1, locking=LOCKING_SOFT):
+                mlp_bf16=1, locking=LOCKING_SOFT, block=1):
     prm = trplk_params(p, q, k, l, tol, max_cycles, seed, SMALLEST, precond, precision, outputs_on_device,
-                       ptr(mlp_weights), (C.c_int * 3)(*grid), int(mlp_bf16), mixed_tol, int(locking))
+                       ptr(mlp_weights), (C.c_int * 3)(*grid), int(mlp_bf16), mixed_tol, int(locking), int(block))
     prm._keep = mlp_weights
     return prm
 
 
 def solve(h: Handle, A: trplk_csr, B=None, *, p, q, k, l, tol=1e-8, X0=None, max_cycles=5000, seed=0,
           precond=PRECOND_JACOBI, precision=PRECISION_FP64, mixed_tol=0.0, mlp_weights=None, grid=(0, 0, 0),
-          mlp_bf16=1, locking=LOCKING_SOFT):
+          mlp_bf16=1, locking=LOCKING_SOFT, block=1):
     """Solve with host outputs (numpy); returns (evals, evecs, resid, status, info dict)."""
     n = A.n
     evals = np.zeros(p)
@@ -352,7 +358,7 @@ def solve(h: Handle, A: trplk_csr, B=None, *, p, q, k, l, tol=1e-8, X0=None, max
     resid = np.zeros(p)
     info = trplk_info()
     params = make_params(p, q, k, l, tol, max_cycles, seed, precond, precision, 0, mixed_tol, mlp_weights, grid,
-                         mlp_bf16, locking)
+                         mlp_bf16, locking, block)
     X0c = None
     if X0 is not None:
         X0c = X0 if _is_device(X0) else np.ascontiguousarray(np.asarray(X0, np.float64).T)

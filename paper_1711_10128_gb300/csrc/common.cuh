@@ -277,6 +277,20 @@ void launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sm
   cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// The same launch in plain stream order (the kernel starts after the previous
+// one has finished).
+template <typename... KArgs, typename... Args>
+void launch_plain(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                  Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cfg.numAttrs = 0;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // ----------------------------------------------------------------- device: grid reduction
 // Deterministic two-stage reduction: every CTA writes `n` partial values, the
 // last CTA to finish sums them in CTA order.  `counter` must be zero on entry

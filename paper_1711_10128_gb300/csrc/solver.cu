@@ -333,6 +333,7 @@ struct Solver {
   // vectors; T, the Rayleigh-Ritz step and the restart act on the active
   // columns [nq, ...) while every orthogonalisation also covers the locked
   // ones.  The active Ritz values sit at theta + toff until the next RR.
+  int blk = 1;                  // block TRPL+K: targets per cycle (1: Algorithm 1)
   bool hard_lock = false;
   int nq = 0, toff = 0;
   std::vector<double> lam_q;    // locked Ritz values
@@ -622,26 +623,50 @@ struct Solver {
           ts_project<S>(c, ld, w0, U[cur], col(AU[cur], w0 - 1), T + (size_t)(w0 - 1) * ldT);
         }
       }
+      // the cycle's targets t .. t+b-1 (capped at p_hat - 1) and their shifts
+      // (block TRPL+K; b = 1 is Algorithm 1)
+      int tg[kMaxK];
+      double rhos[kMaxK];
+      for (int i = 0; i < blk; ++i) {
+        tg[i] = std::min(t + i, k - nq - 1);
+        rhos[i] = th[tg[i]];
+      }
       // first Lanczos vector u = M (A x_t - rho B x_t)  (Algorithm 1, restart)
-      precond_residual(cur, t);
+      precond_residual(cur, tg[0]);
       out.prec++;
       ts_project<S>(c, ld, w0, BU[cur], v, h1);
       orthonormalize_tail(cur, w0, 0, out);
       const int m = q - w0 - nprev;
       int w = w0;
-      // inner preconditioned Lanczos with the T update (eq. (UpdateT))
+      // inner preconditioned Lanczos with the T update (eq. (UpdateT)); with
+      // b > 1 the first b vectors are the targets' preconditioned residuals
+      // and column a >= b is formed from column a - b with the shift of its
+      // sequence a mod b
       for (int j = 0; j < m; ++j) {
         append(cur, w, out);
         ++w;
         if (j < m - 1) {
-          if (MG) {   // M = G^T G, then the fused pass with the preconditioned vector given
-            axpby_shift<S>(c, ld, col(AU[cur], w - 1), col(BU[cur], w - 1), rho, rtmp);
-            apply_fsai(rtmp, v);
-            ts_inner<S>(c, ld, w, U[cur], BU[cur], col(AU[cur], w - 1), col(BU[cur], w - 1), nullptr, PM_GIVEN, rho,
-                        v, T + (size_t)(w - 1) * ldT, h1);
+          const int a1 = j + 1;   // the next column of the cycle
+          double* tcol = T + (size_t)(w - 1) * ldT;
+          if (a1 < blk) {   // restart vector of the next target; the pass forms column w-1's T entries
+            precond_residual(cur, tg[a1]);
+            ts_inner<S>(c, ld, w, U[cur], BU[cur], col(AU[cur], w - 1), col(BU[cur], w - 1), nullptr, PM_GIVEN, 0.0,
+                        v, tcol, h1);
           } else {
-            ts_inner<S>(c, ld, w, U[cur], BU[cur], col(AU[cur], w - 1), col(BU[cur], w - 1), dinv, pmode, rho, v,
-                        T + (size_t)(w - 1) * ldT, h1);
+            const int src = w0 + a1 - blk;   // == w - 1 when b = 1
+            const double shift = rhos[a1 % blk];
+            if (MG) {   // M = G^T G (or IC(0)), then the fused pass with the preconditioned vector given
+              axpby_shift<S>(c, ld, col(AU[cur], src), col(BU[cur], src), shift, rtmp);
+              apply_fsai(rtmp, v);
+              ts_inner<S>(c, ld, w, U[cur], BU[cur], col(AU[cur], w - 1), col(BU[cur], w - 1), nullptr, PM_GIVEN,
+                          shift, v, tcol, h1);
+            } else if (src == w - 1) {
+              ts_inner<S>(c, ld, w, U[cur], BU[cur], col(AU[cur], w - 1), col(BU[cur], w - 1), dinv, pmode, shift, v,
+                          tcol, h1);
+            } else {
+              ts_inner<S>(c, ld, w, U[cur], BU[cur], col(AU[cur], w - 1), col(BU[cur], w - 1), dinv, pmode, shift, v,
+                          tcol, h1, col(AU[cur], src), col(BU[cur], src));
+            }
           }
           out.prec++;
           orthonormalize_tail(cur, w, j + 1, out);
@@ -791,6 +816,9 @@ void validate_params(const trplk_params* P, int64_t n) {
     throw Error(TRPLK_EINVAL, "unsupported preconditioner");
   if (P->locking != TRPLK_LOCKING_SOFT && P->locking != TRPLK_LOCKING_HARD)
     throw Error(TRPLK_EINVAL, "unknown locking mode");
+  const int blk = P->block < 1 ? 1 : P->block;
+  if (blk > P->k || P->k + blk + P->l > P->q) throw Error(TRPLK_EINVAL, "need block <= k and k + block + l <= q");
+  if (blk > 1 && P->locking == TRPLK_LOCKING_HARD) throw Error(TRPLK_EINVAL, "block TRPL+K runs with soft locking");
   if (P->precond == TRPLK_PRECOND_FSAI_LEARNED && !P->mlp_weights)
     throw Error(TRPLK_EINVAL, "learned FSAI needs mlp_weights");
   if (P->precision != TRPLK_PRECISION_FP64 && P->precision != TRPLK_PRECISION_MIXED)
@@ -925,6 +953,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
       Solver<double> S(h, "f64", n, P->p, P->q, P->k, P->l, P->tol, P->max_cycles, Aop, Bop, hasB, dinv64, pmode);
       if (fsai.ok) { S.MG = &fsai.G; S.MGT = &fsai.GT; S.ic0_dinv = fsai.dinv; }
       S.hard_lock = hard;
+      S.blk = P->block < 1 ? 1 : P->block;
       if (shifted) { S.diagA = diagA; S.diagB = diagB; S.dinv_var = dinv64; }
       res = S.run(X0d);
       inf.cycles = res.cycles;
@@ -946,6 +975,7 @@ trplk_status trplk_solve(trplk_handle* h, const trplk_csr* A, const trplk_csr* B
       S32.stall_window = 30;
       if (fsai.ok) { S32.MG = &fsai.Gf; S32.MGT = &fsai.GTf; S32.ic0_dinv = fsai.dinvf; }
       S32.hard_lock = hard;
+      S32.blk = P->block < 1 ? 1 : P->block;
       if (shifted) { S32.diagA = diagA; S32.diagB = diagB; S32.dinv_var = dinv32; }
       SolveOut r32 = S32.run(X0d);
       inf.locked = r32.locked;
@@ -1137,6 +1167,19 @@ trplk_status trplk_rotate(trplk_handle* h, int dtype, int64_t n, int64_t ld, int
       throw Error(TRPLK_EINVAL, "bad arguments");
     h->clear_status();
     TRPLK_DISPATCH(dtype, ts_rotate<S>(h->ctx, ld, w, k, (const S*)U, Y, ldY, (S*)Xout));
+    check_flags(h, 0);
+    return TRPLK_OK;
+  });
+}
+
+trplk_status trplk_rotate_tc(trplk_handle* h, int64_t n, int64_t ld, int w, int k, const float* U, const double* Y,
+                             int ldY, float* Xout) {
+  return guarded(h, [&]() -> trplk_status {
+    check_ld(n, ld);
+    if (!rotate_tc_fits(w, k) || ldY < w || !U || !Y || !Xout || (const void*)U == (const void*)Xout)
+      throw Error(TRPLK_EINVAL, "bad arguments");
+    h->clear_status();
+    rotate_tc(h->ctx, ld, w, k, U, Y, ldY, Xout);
     check_flags(h, 0);
     return TRPLK_OK;
   });

@@ -13,11 +13,12 @@
 // CSR, so the whole block is one contiguous range), then each thread forms its
 // row's dot product from shared memory, gathering x through the read-only
 // cache (for the stencil and FEM operators the gathered x lines are reused
-// from L1/L2 by the neighbouring rows).  Every matvec kernel is launched as a
-// programmatic dependent of the previous kernel on the stream (it waits for
-// it before touching memory, but its launch overlaps that kernel's tail); it
-// lets its own dependents start only at exit, since a kernel whose CTAs
-// became resident early would hold SM resources this many-CTA grid needs.
+// from L1/L2 by the neighbouring rows).  The matvecs are launched in plain
+// stream order: launched as programmatic dependents they cost 4-10% of the
+// Chung-Lu solve (their many-CTA grids were held back by resident CTAs of the
+// neighbouring kernels), while the streaming passes gain from it.  They still
+// begin with grid_dependency_wait() (a no-op in plain order), so either launch
+// is correct.
 // No warp-shuffle reductions: on this
 // GPU a shuffle-and-add tree in FP64 costs more FP64 instructions than the
 // products themselves.  A block whose rows hold more nonzeros than the
@@ -270,10 +271,10 @@ void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const doubl
     ProfScope ps(c, prof_kind<S>(scaled ? PK_SPMV_SCALED : PK_SPMV), bytes);
     const unsigned gb = (unsigned)((A.n + 255) / 256);
     if (scaled)
-      launch_dependent(dia_spmv_kernel<S, true>, dim3(gb), dim3(256), 0, c.stream, A.n, A.dia_ld, A.ndiag, off,
+      launch_plain(dia_spmv_kernel<S, true>, dim3(gb), dim3(256), 0, c.stream, A.n, A.dia_ld, A.ndiag, off,
                        A.dia_val, x, y, scale, g, bx, bg);
     else
-      launch_dependent(dia_spmv_kernel<S, false>, dim3(gb), dim3(256), 0, c.stream, A.n, A.dia_ld, A.ndiag, off,
+      launch_plain(dia_spmv_kernel<S, false>, dim3(gb), dim3(256), 0, c.stream, A.n, A.dia_ld, A.ndiag, off,
                        A.dia_val, x, y, (const double*)nullptr, (S*)nullptr, (const S*)nullptr, (S*)nullptr);
     check_launch("dia_spmv_kernel");
     return;
@@ -293,7 +294,7 @@ void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const doubl
     ProfScope ps(c, prof_kind<S>(scaled ? PK_SPMV_SCALED : PK_SPMV), bytes);
     const unsigned gb = (unsigned)(blocks > 0 ? blocks : 1);
 #define TRPLK_SELL(SC, HY)                                                                                  \
-  launch_dependent(sell_spmv_kernel<S, SC, HY>, dim3(gb), dim3(256), 0, c.stream, m, nslices, A.sl_ptr,      \
+  launch_plain(sell_spmv_kernel<S, SC, HY>, dim3(gb), dim3(256), 0, c.stream, m, nslices, A.sl_ptr,      \
                    A.sl_col, A.sl_val, A.sl_perm, A.long_rows, A.n_long_cta, A.n_long_warp, A.rowptr, A.col,  \
                    A.val, x, y, scale, g, bx, bg)
     if (scaled) {
@@ -316,11 +317,11 @@ void spmv_launch(const Ctx& c, const DevCsr<S>& A, const S* x, S* y, const doubl
   ProfScope ps(c, prof_kind<S>(scaled ? PK_SPMV_SCALED : PK_SPMV), bytes);
   if (scaled) {
     smem_optin<spmv_kernel<S, true>>((int)smem, c.device);
-    launch_dependent(spmv_kernel<S, true>, dim3((unsigned)blocks), dim3(kRows), smem, c.stream, A.n, A.rowptr, A.col,
+    launch_plain(spmv_kernel<S, true>, dim3((unsigned)blocks), dim3(kRows), smem, c.stream, A.n, A.rowptr, A.col,
                      A.val, x, y, scale, g, bx, bg);
   } else {
     smem_optin<spmv_kernel<S, false>>((int)smem, c.device);
-    launch_dependent(spmv_kernel<S, false>, dim3((unsigned)blocks), dim3(kRows), smem, c.stream, A.n, A.rowptr,
+    launch_plain(spmv_kernel<S, false>, dim3((unsigned)blocks), dim3(kRows), smem, c.stream, A.n, A.rowptr,
                      A.col, A.val, x, y, (const double*)nullptr, (S*)nullptr, (const S*)nullptr, (S*)nullptr);
   }
   check_launch("spmv_kernel");

@@ -38,7 +38,8 @@ namespace trplk {
 
 enum TSKind : int {
   TS_PROJ = 0,     // out0 = mat0^T vec0                                   (1 RHS)
-  TS_INNER = 1,    // v = M(z - rho bg); out0 = mat0^T z; out1 = mat1^T v  (2 RHS)
+  TS_INNER = 1,    // v = M(zs - rho bs); out0 = mat0^T z; out1 = mat1^T v  (2 RHS;
+                   // zs, bs = z, bg, or the staged vectors vsrc, bsrc in block TRPL+K)
   TS_UPDPROJ = 2,  // v' = v - mat0 h; out0 = mat1^T v'
   TS_UPDNORM = 3,  // v' = v - mat0 h; out0 = ||v'||^2 -> beta, 1/beta, breakdown test
   TS_UPD = 4,      // v' = v - mat0 h
@@ -78,8 +79,9 @@ struct TSArgs {
   const S* mat[3];     // staged matrices, w columns each (ld)
   int nmat;            // number of distinct staged matrices
   int matsel[3];       // which staged matrix plays operand 0/1/2 of the kind
-  const S* vec[3];     // staged vectors
+  const S* vec[5];     // staged vectors
   int nvec;
+  int vsrc, bsrc;      // TS_INNER: staged vectors the new Lanczos vector is formed from (0, 1: z and bg)
   int w;               // columns of each staged matrix
   int64_t ld;
   int ntiles;
@@ -315,13 +317,16 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
             if (a.pmode == PM_GIVEN) {
               vq[h] = ld4(vst + TR + i);
             } else {
-              const V4<S> bg = ld4(vst + TR + i);
+              // the source of the new vector: the just-multiplied column (z, bg)
+              // or, in block TRPL+K, the column of the same sequence b back
+              const V4<S> zs = a.vsrc ? ld4(vst + a.vsrc * TR + i) : zq[h];
+              const V4<S> bg = ld4(vst + a.bsrc * TR + i);
               const S rho = (S)a.rho;
               V4<S> v;
-              v.x = zq[h].x - rho * bg.x;
-              v.y = zq[h].y - rho * bg.y;
-              v.z = zq[h].z - rho * bg.z;
-              v.w = zq[h].w - rho * bg.w;
+              v.x = zs.x - rho * bg.x;
+              v.y = zs.y - rho * bg.y;
+              v.z = zs.z - rho * bg.z;
+              v.w = zs.w - rho * bg.w;
               if (a.pmode == PM_JACOBI) {
                 const V4<S> dv = ld4(vst + 2 * TR + i);
                 v.x *= dv.x;

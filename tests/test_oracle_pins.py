@@ -461,3 +461,59 @@ def test_one_previous_vector_cuts_matvecs_for_five_pairs():
     x0 = W.start_block(A.n, 8, 12)
     mv = {l: O.solve(As, None, 5, 18, 8, l, 1e-8, x0, "none")["mv_A"] for l in (0, 1)}
     assert mv[1] < 0.9 * mv[0], mv
+
+
+# ---------------------------------------------------------------- block TRPL+K (R15)
+def test_block_first_cycle_spans_the_block_krylov_space():
+    """With M = I and no +K vectors, the first cycle of block TRPL+K (b = 2)
+    builds span [X, R, C R, C^2 R, ...] with R the residuals of the two
+    targets and C = (I - X X^T) A the projected operator of Sec. 3 (the block
+    Krylov space; the shifts do not change it): every basis column lies in the
+    explicitly built space, column block by column block."""
+    A = W.diffusion_3d(7, W.lognormal_field(7, 1.0, 2)).to_scipy()
+    n = A.shape[0]
+    p, q, k, b = 2, 14, 4, 2
+    X0 = W.start_block(n, k, 3)
+    r = O.solve(A, None, p, q, k, 0, 1e-14, X0, "none", max_cycles=1, record=True, block=b)
+    tr = r["trace"][0]
+    U = tr["U"]
+    X, AX, _, theta, _, _ = O.initial_rayleigh_ritz(A, lambda v: v.copy(), X0)
+    R = AX[:, :b] - X[:, :b] * theta[:b]
+    blocks = [X, R]
+    while sum(Z.shape[1] for Z in blocks) < U.shape[1]:
+        Z = A @ blocks[-1]
+        blocks.append(Z - X @ (X.T @ Z))
+    Kall = np.hstack(blocks)
+    assert U.shape[1] == q
+    for c in range(k, q + 1):
+        K = np.linalg.qr(Kall[:, :c])[0]
+        assert np.linalg.norm(U[:, :c] - K @ (K.T @ U[:, :c])) <= 1e-9 * np.sqrt(c), c
+
+
+def test_block_closed_form_degenerate_pairs_and_accounting():
+    """Block TRPL+K (b = 2) on the 2D Laplacian, whose wanted set holds
+    exactly degenerate pairs: closed-form eigenvalues, orthonormal vectors,
+    and p_hat + (q - p_hat) matvecs per cycle."""
+    N = 24
+    A = W.laplacian_2d(N).to_scipy()
+    p, q, k, l = 6, 20, 8, 1
+    r = O.solve(A, None, p, q, k, l, 1e-10, W.start_block(A.shape[0], k, 2), "jacobi", block=2)
+    assert r["status"] == O.OK
+    lam = lap2d_eigs(N, p)
+    assert np.all(np.abs(r["evals"] - lam) <= 1e-9 * lam)
+    X = r["evecs"]
+    assert np.allclose(X.T @ X, np.eye(p), atol=1e-10)
+    assert r["mv_A"] == k + (q - k) * r["cycles"]
+
+
+def test_block_generalized_pencil_brute_force():
+    N = 5
+    A, B = W.fem_q1_pencil(N, np.random.default_rng(5).uniform(1, 10, (N, N, N)))
+    As, Bs = A.to_scipy(), B.to_scipy()
+    p, q, k, l = 4, 18, 6, 1
+    r = O.solve(As, Bs, p, q, k, l, 1e-10, W.start_block(A.n, k, 4), "jacobi", block=3)
+    assert r["status"] == O.OK
+    brute = sl.eigh(As.toarray(), Bs.toarray(), eigvals_only=True)[:p]
+    assert np.all(np.abs(r["evals"] - brute) <= 1e-9 * brute)
+    X = r["evecs"]
+    assert np.allclose(X.T @ (Bs @ X), np.eye(p), atol=1e-10)
