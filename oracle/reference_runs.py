@@ -5,7 +5,10 @@ The stored eigenvalues are the FP64 oracle's answer for the full-size
 operators (used as full-size parity references), and the stored cycle counts
 and per-phase timings let the CPU-baseline measurement extrapolate a bounded
 sample of the oracle to a whole solve.  Calls only ``oracle/`` and the seeded
-input generators.  Usage: python -m oracle.reference_runs [name ...]
+input generators.  Usage:
+  python -m oracle.reference_runs [name ...]                  run and store
+  python -m oracle.reference_runs --time-on-this-host NAME OUT.json
+  python -m oracle.reference_runs --add-host-timing OUT.json  add that run's timing
 """
 from __future__ import annotations
 
@@ -77,5 +80,35 @@ def main(names):
         print(name, data[name]["status"], data[name]["cycles"], data[name]["seconds"], flush=True)
 
 
+def time_on_this_host(name, path):
+    """Run one workload to convergence and write the run alone to `path` (for
+    timing the oracle on another machine without touching the stored runs)."""
+    r = run(name)
+    r["workload"] = name
+    json.dump(r, open(path, "w"), indent=1)
+    print(name, r["status"], r["cycles"], r["seconds"], r["host"], flush=True)
+
+
+def add_host_timing(path):
+    """Record a run written by `time_on_this_host` as an extra timing of its
+    stored workload: host, seconds, cycles, and the largest relative
+    difference of its eigenvalues from the stored ones."""
+    r = json.load(open(path))
+    data = json.load(open(OUT))
+    ent = data[r["workload"]]
+    ev, ref = np.array(r["evals"]), np.array(ent["evals"])
+    timing = dict(host=r["host"], seconds=r["seconds"], cores=r["cores"], cycles=r["cycles"], mv_A=r["mv_A"],
+                  status=r["status"], max_rel_eval_diff=float(np.max(np.abs(ev - ref) / np.abs(ref))))
+    ent["other_host_timings"] = [t for t in ent.get("other_host_timings", []) if t["host"] != timing["host"]]
+    ent["other_host_timings"].append(timing)
+    json.dump(data, open(OUT, "w"), indent=1)
+    print(r["workload"], timing, flush=True)
+
+
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["laplace100", "diffusion128"])
+    if len(sys.argv) == 4 and sys.argv[1] == "--time-on-this-host":
+        time_on_this_host(sys.argv[2], sys.argv[3])
+    elif len(sys.argv) == 3 and sys.argv[1] == "--add-host-timing":
+        add_host_timing(sys.argv[2])
+    else:
+        main(sys.argv[1:] or ["laplace100", "diffusion128"])
