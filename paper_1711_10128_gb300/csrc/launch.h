@@ -219,7 +219,8 @@ template <typename S>
 void axpby_shift(const Ctx& c, int64_t ld, const S* x, const S* y, double rho, S* r);
 
 // ---- Rayleigh-Ritz (rr.cu): eigenpairs of the w x w symmetric T (upper
-// triangle read), theta ascending, Y (ld = w) sign-normalised.
-void rayleigh_ritz(const Ctx& c, int w, const double* T, int ldT, double* theta, double* Y);
+// triangle read), theta ascending, Y (ld = w) sign-normalised; fp32_data: T
+// comes from FP32 data, eigenpairs to 1e-10 ||T||_F instead of FP64 rounding.
+void rayleigh_ritz(const Ctx& c, int w, const double* T, int ldT, double* theta, double* Y, bool fp32_data = false);
 
 }  // namespace trplk

@@ -475,7 +475,7 @@ struct Solver {
   int rr_and_restart(int cur, int w) {
     const int wa = w - nq, ka = k - nq;
     const size_t o = (size_t)nq * ld;
-    rayleigh_ritz(c, wa, T + (size_t)nq * ldT + nq, ldT, theta, Y);
+    rayleigh_ritz(c, wa, T + (size_t)nq * ldT + nq, ldT, theta, Y, sizeof(S) == 4);
     toff = 0;
     const int nx = 1 - cur;
     ts_rotate<S>(c, ld, wa, ka, U[cur] + o, Y, wa, U[nx] + o);

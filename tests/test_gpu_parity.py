@@ -345,6 +345,34 @@ def test_rayleigh_ritz_diagonal_and_degenerate(lib, h):
     assert np.allclose(T @ Yh, Yh * th.cpu().numpy(), atol=0)
 
 
+@pytest.mark.parametrize("w", [24, 40, 64])
+def test_rayleigh_ritz_clustered_spectrum(lib, h, w):
+    """The spectrum of a thick-restart T on a power-law graph: Ritz values from
+    1e-3 to 1e4, with a pair 1e-9 apart (relative), an exact double and a
+    triple 1e-12 ||T|| apart, in a random orthogonal basis.  Eigenvectors inside
+    a cluster are not unique, so they are checked through invariants: the
+    eigenvalues against LAPACK's to 1e-13 ||T||, Y orthonormal to 1e-13, and
+    T Y = Y Theta to 1e-13 ||T||."""
+    rng = np.random.default_rng(100 + w)
+    d = np.sort(10.0 ** rng.uniform(-3, 4, w))
+    top = d.max()
+    d[1] = d[0] * (1 + 1e-9)
+    d[3] = d[2]
+    d[5], d[6] = d[4] + 1e-12 * top, d[4] + 2e-12 * top
+    Q = np.linalg.qr(rng.standard_normal((w, w)))[0]
+    T = (Q * d) @ Q.T
+    T = (T + T.T) / 2
+    th = torch.zeros(w, dtype=torch.float64, device="cuda")
+    Y = torch.zeros(w * w, dtype=torch.float64, device="cuda")
+    lib.trplk_rayleigh_ritz(h, w, torch.from_numpy(np.asfortranarray(T).ravel(order="F")).cuda(), w, th, Y)
+    thh = th.cpu().numpy()
+    Yh = Y.cpu().numpy().reshape(w, w).T
+    assert np.all(np.diff(thh) >= 0)
+    assert np.abs(thh - np.linalg.eigvalsh(T)).max() <= 1e-13 * top
+    assert np.abs(Yh.T @ Yh - np.eye(w)).max() <= 1e-13
+    assert np.abs(T @ Yh - Yh * thh).max() <= 1e-13 * top
+
+
 # ---------------------------------------------------------------- a7 rotation + residuals
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_rotate_and_residual_norms(lib, h, prec):
