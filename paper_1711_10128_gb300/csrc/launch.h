@@ -179,7 +179,8 @@ template <typename S>
 void ts_dot_norm(const Ctx& c, int64_t ld, const S* v, const S* bv, const double* h1,
                  const double* h2, int w, double* beta2, double* scale, double eps_breakdown);
 template <typename S>
-void ts_rotate(const Ctx& c, int64_t ld, int w, int k, const S* U, const double* Y, int ldY, S* X);
+void ts_rotate(const Ctx& c, int64_t ld, int w, int k, const S* U, const double* Y, int ldY, S* X,
+               bool tensor_cores = true);
 template <typename S>
 void ts_resid(const Ctx& c, int64_t ld, int k, const S* X, const S* AX, const S* BX,
               const double* theta, double* rnorm, double* xnorm);

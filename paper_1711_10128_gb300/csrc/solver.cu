@@ -478,9 +478,12 @@ struct Solver {
     rayleigh_ritz(c, wa, T + (size_t)nq * ldT + nq, ldT, theta, Y, sizeof(S) == 4);
     toff = 0;
     const int nx = 1 - cur;
-    ts_rotate<S>(c, ld, wa, ka, U[cur] + o, Y, wa, U[nx] + o);
-    ts_rotate<S>(c, ld, wa, ka, AU[cur] + o, Y, wa, AU[nx] + o);
-    if (hasB) ts_rotate<S>(c, ld, wa, ka, BU[cur] + o, Y, wa, BU[nx] + o);
+    // The tensor-core rotation (FP32 data, B = I): on the Q1 pencil the FP32
+    // phase with it left the FP64 refinement 37 cycles instead of 21
+    // (n = 884,736, w = 50, k = 25), so pencils keep the CUDA-core rotation.
+    ts_rotate<S>(c, ld, wa, ka, U[cur] + o, Y, wa, U[nx] + o, !hasB);
+    ts_rotate<S>(c, ld, wa, ka, AU[cur] + o, Y, wa, AU[nx] + o, !hasB);
+    if (hasB) ts_rotate<S>(c, ld, wa, ka, BU[cur] + o, Y, wa, BU[nx] + o, false);
     ts_resid<S>(c, ld, ka, U[nx] + o, AU[nx] + o, hasB ? BU[nx] + o : nullptr, theta, rn, xn);
     return nx;
   }

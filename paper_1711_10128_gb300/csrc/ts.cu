@@ -205,10 +205,11 @@ void ts_dot_norm(const Ctx& c, int64_t ld, const S* v, const S* bv, const double
 }
 
 template <typename S>
-void ts_rotate(const Ctx& c, int64_t ld, int w, int k, const S* U, const double* Y, int ldY, S* X) {
+void ts_rotate(const Ctx& c, int64_t ld, int w, int k, const S* U, const double* Y, int ldY, S* X,
+               bool tensor_cores) {
   if (k > kMaxK) throw Error(TRPLK_EINVAL, "rotation width exceeds 32");
   if constexpr (sizeof(S) == 4) {
-    if (rotate_tc_preferred(w, k)) {
+    if (tensor_cores && rotate_tc_preferred(w, k)) {
       rotate_tc(c, ld, w, k, U, Y, ldY, X);
       return;
     }
@@ -245,7 +246,7 @@ void ts_resid(const Ctx& c, int64_t ld, int k, const S* X, const S* AX, const S*
   template void ts_update<S>(const Ctx&, int64_t, int, const S*, const double*, S*);                  \
   template void ts_dot_norm<S>(const Ctx&, int64_t, const S*, const S*, const double*, const double*, \
                                int, double*, double*, double);                                        \
-  template void ts_rotate<S>(const Ctx&, int64_t, int, int, const S*, const double*, int, S*);        \
+  template void ts_rotate<S>(const Ctx&, int64_t, int, int, const S*, const double*, int, S*, bool);  \
   template void ts_resid<S>(const Ctx&, int64_t, int, const S*, const S*, const S*, const double*,    \
                             double*, double*);
 
