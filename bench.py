@@ -48,17 +48,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # the default: 3D 7-point lognormal(0, 1) diffusion on 128^3, Jacobi
+    # 3D 7-point lognormal(0, 1) diffusion on 128^3, Jacobi
     "diffusion128": dict(name="diffusion3d_128_lognormal", N=128, sigma=1.0, coef_seed=1, p=10, q=40, k=15, l=1,
                          tol=1e-8, seed=0, precond="jacobi"),
     # trilinear Q1 stiffness/mass pencil on 96^3 elements, E ~ U[1, 10] (seed 2), Jacobi on A
     "q1pencil96": dict(name="q1_fem_pencil_96", N=96, E_seed=2, p=20, q=50, k=25, l=1, tol=1e-8, seed=0,
                        precond="jacobi"),
-    # L + 1e-3 I of a Chung-Lu graph, 2^22 vertices, mean degree 16, gamma 2.1 (seed 3), largest component
+    # the default: L + 1e-3 I of a Chung-Lu graph, 2^22 vertices, mean degree 16, gamma 2.1 (seed 3),
+    # largest component
     "chunglu22": dict(name="chung_lu_laplacian_2^22_lcc", n=1 << 22, mean=16.0, gamma=2.1, graph_seed=3, p=16, q=40,
                       k=20, l=1, tol=1e-8, seed=0, precond="jacobi"),
+    # the same graph family on 2^20 vertices: the size profiler captures of the power-law matvec and the
+    # basis passes run on (matrix and basis columns still larger than L2, about 1 GB on the device)
+    "chunglu20": dict(name="chung_lu_laplacian_2^20_lcc", n=1 << 20, mean=16.0, gamma=2.1, graph_seed=3, p=16, q=40,
+                      k=20, l=1, tol=1e-8, seed=0, precond="jacobi"),
     # anisotropic 7-point diffusion on 128^3 (held-out operator, seed 2000): learned FSAI trained on
-    # twelve 32^3 operators of the same family (seeds 1000-1011), against Jacobi and classical FSAI
+    # 200 32^3 operators of the same family (seeds 1000-1199), against Jacobi and classical FSAI
     "aniso128": dict(name="anisotropic_diffusion_128_learned_fsai", N=128, op_seed=2000, train_N=32,
                      train_seeds=list(range(1000, 1200)), p=20, q=50, k=25, l=1, tol=1e-8, seed=0,
                      precond="fsai_learned"),
@@ -81,6 +86,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
                     help="chunglu22 is the headline; the others measure the remaining operator classes")
+    ap.add_argument("--profile-solves", type=int, default=0,
+                    help="run this many mixed solves of the workload with the library's per-kernel profiler on, "
+                         "print the per-family launches, time and algorithmic bytes as one JSON line and exit "
+                         "(the command profiler captures run; nothing else is timed)")
     ap.add_argument("--learned-ops", type=int, default=len(HELD_OUT_SEEDS),
                     help="held-out anisotropic 128^3 operators of the learned block (0 skips it)")
     args = ap.parse_args()
@@ -512,6 +521,22 @@ def run_ours(args, world, rank, local, pg):
         torch.cuda.synchronize(dev)
         barrier(pg, local)
         return ms, infos, prof, clocks
+
+    if args.profile_solves > 0:
+        lib.trplk_profile(h, 1)
+        for _ in range(args.profile_solves):
+            rc, info = solve_device(lib.PRECISION_MIXED, P["precond"])
+            if rc != lib.OK:
+                raise RuntimeError(f"solve did not converge: {info}")
+        torch.cuda.synchronize(dev)
+        prof = lib.profile_summary(h)
+        lib.trplk_profile(h, 0)
+        h.close()
+        if rank == 0:
+            print(json.dumps({"workload": P["key"], "solves": args.profile_solves, "solve": info,
+                              "families": {k: {"launches": v[0], "ms": v[1], "algorithmic_bytes": v[2]}
+                                           for k, v in prof.items()}}), flush=True)
+        return 0
 
     # headline: mixed path, inputs resident in HBM, no profiler in the timed loop
     ms_mixed, infos, _, clocks = timed(lib.PRECISION_MIXED, P["precond"], args.steps, args.warmup)

@@ -1,23 +1,34 @@
-"""Record the DRAM traffic of a kernel family from an ncu capture.
+"""DRAM traffic and launch list of the solver's kernel families from one ncu capture.
 
 The bench reports `roofline.traffic`, the DRAM bytes one launch of the
 dominant kernel family moves, as the DRAM-bytes-per-algorithmic-byte ratio
-measured by ncu times the launch's algorithmic bytes.  This script computes
-that ratio from the raw page of an ncu report (`ncu -i REPORT --page raw
---csv`) for the launches whose kernel name matches a pattern, given the
-algorithmic bytes of those launches, and stores it in profiles/traffic.json
-under "<workload>/<family>" together with the sha256 of the kernel sources it
-was measured on; the bench withdraws the figure (reports null) as soon as any
-of those sources changes.
+that ncu measured for that family times the launch's algorithmic bytes.  This
+script computes those ratios.  It reads two files made by the same command:
+
+  * the raw page of an ncu capture of every kernel the command launches
+    (`ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+    --csv --page raw --log-file RAW.csv python bench.py --profile-solves N ...`);
+  * the JSON line the same command prints without ncu (the library profiler's
+    launches and algorithmic bytes per kernel family for those N solves).
+
+Every ncu launch is assigned to the profiler family its kernel belongs to
+(template arguments name the precision, the matvec's scaled form and the
+streaming pass's kind); for a family whose launch counts agree, the ratio
+sum(DRAM bytes) / sum(algorithmic bytes) goes to profiles/traffic.json under
+"<workload>/<family>", with the sha256 of the kernel sources it was measured
+on: the bench withdraws the figure (reports null) once any of them changes.
+With --launches-md it also writes the launch list (per kernel family:
+launches, total device time, share) as a Markdown summary.
 
 Usage:
-  python -m paper_1711_10128_gb300.traffic RAW.csv WORKLOAD FAMILY KERNEL_REGEX ALG_BYTES_PER_LAUNCH \\
-      SOURCE [SOURCE ...] --command "the ncu command line"
+  python -m paper_1711_10128_gb300.traffic RAW.csv PROFILE.json --command "the ncu command" \\
+      [--launches-md profiles/launches_<kernel>_<workload>.md]
 """
 from __future__ import annotations
 
 import argparse
 import csv
+import glob
 import hashlib
 import json
 import os
@@ -25,62 +36,145 @@ import re
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 OUT = os.path.join(ROOT, "profiles", "traffic.json")
+CSRC = os.path.join("paper_1711_10128_gb300", "csrc")
+TS_KINDS = ["ts_project", "ts_inner", "ts_update_project", "ts_update_norm", "ts_update", "ts_rotate", "ts_resid",
+            "ts_dot"]
+SCALE = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1.0, "usecond": 1e3, "msecond": 1e6,
+         "ns": 1.0, "us": 1e3, "ms": 1e6, "second": 1e9, "s": 1e9}
 
 
-def _num(s):
-    return float(s.replace(",", "")) if s not in ("", "n/a") else None
+def _flag(s):
+    return s.strip() in ("1", "true")
 
 
-def launches(raw_csv, kernel_regex):
-    """(kernel name, dram read bytes, dram write bytes, duration ns) of every
-    matching launch in an ncu raw CSV page."""
+def family_of(name):
+    """The library profiler's family of a kernel (by its demangled name), or
+    None for kernels outside the families (setup, conversions, reductions)."""
+    suffix = lambda prec: "_f64" if prec == "double" else ""
+    m = re.search(r"ts_kernel<(float|double),\s*(?:\(int\))?(\d+),", name)
+    if m:
+        return TS_KINDS[int(m.group(2))] + suffix(m.group(1))
+    m = re.search(r"(?:sell_spmv_kernel|dia_spmv_kernel|\bspmv_kernel)<(float|double),\s*(\w+)", name)
+    if m:
+        return ("spmv_scaled" if _flag(m.group(2)) else "spmv") + suffix(m.group(1))
+    if "rotate_tc_kernel" in name:
+        return "ts_rotate"
+    if "rr_kernel" in name:
+        return "rayleigh_ritz"
+    return None
+
+
+METRICS = ("gpu__time_duration.sum", "dram__bytes_read.sum", "dram__bytes_write.sum")
+
+
+def read_launches(raw_csv):
+    """(kernel name, family, duration ns, dram read bytes, dram write bytes)
+    for every launch of an ncu CSV (the raw page: a row per launch; or the
+    details page: a row per launch and metric); missing metrics are None."""
     rows = list(csv.reader(open(raw_csv)))
-    hdr, units = rows[0], rows[1]
+    start = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[start]
     col = {h: i for i, h in enumerate(hdr)}
-    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1.0, "usecond": 1e3,
-             "msecond": 1e6, "ns": 1.0, "us": 1e3, "ms": 1e6}
+    if "Metric Name" in col:   # details page
+        per = {}
+        for r in rows[start + 1:]:
+            if len(r) != len(hdr) or r[col["Metric Name"]] not in METRICS:
+                continue
+            key = r[col["ID"]]
+            e = per.setdefault(key, {"name": r[col["Kernel Name"]]})
+            v = r[col["Metric Value"]].replace(",", "")
+            e[r[col["Metric Name"]]] = float(v) * SCALE.get(r[col["Metric Unit"]], 1.0) if v not in ("", "n/a") else None
+        out = []
+        for key in sorted(per, key=int):
+            e = per[key]
+            out.append((e["name"], family_of(e["name"]), *[e.get(m) for m in METRICS]))
+        return out
+    units = rows[start + 1]
     out = []
-    for r in rows[2:]:
-        name = r[col["Kernel Name"]]
-        if not re.search(kernel_regex, name):
+    for r in rows[start + 2:]:
+        if len(r) != len(hdr):
             continue
         vals = []
-        for m in ("dram__bytes_read.sum", "dram__bytes_write.sum", "gpu__time_duration.sum"):
-            v = _num(r[col[m]])
-            vals.append(None if v is None else v * scale.get(units[col[m]], 1.0))
-        out.append((name, *vals))
+        for m in METRICS:
+            if m not in col or r[col[m]] in ("", "n/a"):
+                vals.append(None)
+                continue
+            vals.append(float(r[col[m]].replace(",", "")) * SCALE.get(units[col[m]], 1.0))
+        name = r[col["Kernel Name"]]
+        out.append((name, family_of(name), *vals))
     return out
 
 
-def sources_sha(sources):
+def sources():
+    return sorted(os.path.relpath(p, ROOT) for p in glob.glob(os.path.join(ROOT, CSRC, "*"))
+                  if p.endswith((".cu", ".cuh", ".h")))
+
+
+def sources_sha(files):
     h = hashlib.sha256()
-    for f in sources:
+    for f in files:
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()
+
+
+def launch_table(launches, command, workload, solves):
+    tot = sum(t for _, _, t, _, _ in launches if t) or 1.0
+    by = {}
+    for name, fam, t, _, _ in launches:
+        short = re.sub(r"\(.*$", "", name).replace("void ", "").replace("trplk::", "")
+        short = short.replace("(anonymous namespace)::", "").replace("<unnamed>::", "")
+        e = by.setdefault(short, [fam or "-", 0, 0.0])
+        e[1] += 1
+        e[2] += t or 0.0
+    lines = [f"# Launch list: {workload}, {solves} mixed solve(s)", "",
+             "Every kernel launched by the command below, with its device time "
+             "(`gpu__time_duration.sum`, one pass; launches serialised and cold-cache under the profiler, so "
+             "compare shares, not absolute times).", "", "```", command, "```", "",
+             "| kernel | family | launches | total us | share |", "|---|---|---:|---:|---:|"]
+    for short, (fam, n, t) in sorted(by.items(), key=lambda kv: -kv[1][2]):
+        lines.append(f"| `{short}` | {fam} | {n} | {t / 1e3:.1f} | {t / tot:.4f} |")
+    fams = {}
+    for _, fam, t, _, _ in launches:
+        fams[fam or "other"] = fams.get(fam or "other", 0.0) + (t or 0.0)
+    lines += ["", "By family:", "", "| family | share |", "|---|---:|"]
+    for fam, t in sorted(fams.items(), key=lambda kv: -kv[1]):
+        lines.append(f"| {fam} | {t / tot:.4f} |")
+    return "\n".join(lines) + "\n"
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("raw_csv")
-    ap.add_argument("workload")
-    ap.add_argument("family")
-    ap.add_argument("kernel_regex")
-    ap.add_argument("alg_bytes", type=float, help="algorithmic bytes of one captured launch")
-    ap.add_argument("sources", nargs="+")
+    ap.add_argument("profile_json")
     ap.add_argument("--command", required=True)
+    ap.add_argument("--launches-md")
     a = ap.parse_args()
-    ls = launches(a.raw_csv, a.kernel_regex)
-    if not ls:
-        raise SystemExit("no launch matches")
-    caps = [{"kernel": n, "dram_read": r, "dram_write": w, "duration_us": t / 1e3,
-             "dram_per_algorithmic_byte": (r + w) / a.alg_bytes} for n, r, w, t in ls]
-    ratio = sum(c["dram_per_algorithmic_byte"] for c in caps) / len(caps)
+    launches = read_launches(a.raw_csv)
+    prof = json.loads(open(a.profile_json).read().strip().splitlines()[-1])
+    workload = prof["workload"]
+    files = sources()
+    sha = sources_sha(files)
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
-    data[f"{a.workload}/{a.family}"] = {
-        "dram_per_algorithmic_byte": ratio, "algorithmic_bytes_per_launch": a.alg_bytes, "captures": caps,
-        "command": a.command, "sources": a.sources, "sha256": sources_sha(a.sources)}
+    for fam, ent in prof["families"].items():
+        if ent["algorithmic_bytes"] <= 0:
+            continue
+        mine = [l for l in launches if l[1] == fam]
+        if not mine or any(l[3] is None or l[4] is None for l in mine):
+            continue
+        if len(mine) != ent["launches"]:
+            print(f"{fam}: {len(mine)} ncu launches against {ent['launches']} profiled; not recorded")
+            continue
+        dram = sum(l[3] + l[4] for l in mine)
+        ratio = dram / ent["algorithmic_bytes"]
+        data[f"{workload}/{fam}"] = {
+            "dram_per_algorithmic_byte": ratio, "launches": len(mine), "dram_bytes": dram,
+            "algorithmic_bytes": ent["algorithmic_bytes"], "solves": prof["solves"], "command": a.command,
+            "sources": files, "sha256": sha}
+        print(f"{workload}/{fam}: {ratio:.4f} DRAM bytes per algorithmic byte over {len(mine)} launches")
     json.dump(data, open(OUT, "w"), indent=1)
-    print(f"{a.workload}/{a.family}: {ratio:.4f} DRAM bytes per algorithmic byte over {len(caps)} launch(es)")
+    if a.launches_md:
+        open(a.launches_md, "w").write(launch_table(launches, a.command, workload, prof["solves"]))
+        print("wrote", a.launches_md)
 
 
 if __name__ == "__main__":

@@ -52,7 +52,7 @@ def test_eig_error_against_a_stored_run():
 
 
 def test_workload_table():
-    assert set(bench.WORKLOADS) == {"diffusion128", "q1pencil96", "chunglu22", "aniso128"}
+    assert set(bench.WORKLOADS) == {"diffusion128", "q1pencil96", "chunglu22", "chunglu20", "aniso128"}
     for key, w in bench.WORKLOADS.items():
         assert w["p"] <= w["k"] < w["q"] <= 64 and w["l"] >= 0 and w["tol"] == 1e-8, key
     # the headline is the configuration the metric is quoted on (the largest
