@@ -22,7 +22,7 @@ launches, total device time, share) as a Markdown summary.
 
 Usage:
   python -m paper_1711_10128_gb300.traffic RAW.csv PROFILE.json --command "the ncu command" \\
-      [--launches-md profiles/launches_<kernel>_<workload>.md]
+      [--plain "the command without ncu"] [--launches-md profiles/launches_<workload>_mixed.md]
 """
 from __future__ import annotations
 
@@ -44,7 +44,7 @@ SCALE = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1.0, 
 
 
 def _flag(s):
-    return s.strip() in ("1", "true")
+    return s.strip() in ("1", "true", "(bool)1")
 
 
 def family_of(name):
@@ -54,7 +54,7 @@ def family_of(name):
     m = re.search(r"ts_kernel<(float|double),\s*(?:\(int\))?(\d+),", name)
     if m:
         return TS_KINDS[int(m.group(2))] + suffix(m.group(1))
-    m = re.search(r"(?:sell_spmv_kernel|dia_spmv_kernel|\bspmv_kernel)<(float|double),\s*(\w+)", name)
+    m = re.search(r"(?:sell_spmv_kernel|dia_spmv_kernel|\bspmv_kernel)<(float|double),\s*((?:\(bool\))?\w+)", name)
     if m:
         return ("spmv_scaled" if _flag(m.group(2)) else "spmv") + suffix(m.group(1))
     if "rotate_tc_kernel" in name:
@@ -117,7 +117,7 @@ def sources_sha(files):
     return h.hexdigest()
 
 
-def launch_table(launches, command, workload, solves):
+def launch_table(launches, commands, workload, solves):
     tot = sum(t for _, _, t, _, _ in launches if t) or 1.0
     by = {}
     for name, fam, t, _, _ in launches:
@@ -129,7 +129,8 @@ def launch_table(launches, command, workload, solves):
     lines = [f"# Launch list: {workload}, {solves} mixed solve(s)", "",
              "Every kernel launched by the command below, with its device time "
              "(`gpu__time_duration.sum`, one pass; launches serialised and cold-cache under the profiler, so "
-             "compare shares, not absolute times).", "", "```", command, "```", "",
+             "compare shares, not absolute times).  Commands, from the repository root:", "", "```", *commands,
+             "```", "",
              "| kernel | family | launches | total us | share |", "|---|---|---:|---:|---:|"]
     for short, (fam, n, t) in sorted(by.items(), key=lambda kv: -kv[1][2]):
         lines.append(f"| `{short}` | {fam} | {n} | {t / 1e3:.1f} | {t / tot:.4f} |")
@@ -146,7 +147,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("raw_csv")
     ap.add_argument("profile_json")
-    ap.add_argument("--command", required=True)
+    ap.add_argument("--command", required=True, help="the ncu capture command")
+    ap.add_argument("--plain", help="the same command without ncu, whose output is PROFILE.json")
     ap.add_argument("--launches-md")
     a = ap.parse_args()
     launches = read_launches(a.raw_csv)
@@ -173,7 +175,11 @@ def main():
         print(f"{workload}/{fam}: {ratio:.4f} DRAM bytes per algorithmic byte over {len(mine)} launches")
     json.dump(data, open(OUT, "w"), indent=1)
     if a.launches_md:
-        open(a.launches_md, "w").write(launch_table(launches, a.command, workload, prof["solves"]))
+        cmds = ([f"{a.plain} > {a.profile_json}"] if a.plain else []) + [
+            a.command,
+            f"python -m paper_1711_10128_gb300.traffic {a.raw_csv} {a.profile_json} --command '<the ncu line>' "
+            f"--launches-md {a.launches_md}"]
+        open(a.launches_md, "w").write(launch_table(launches, cmds, workload, prof["solves"]))
         print("wrote", a.launches_md)
 
 
