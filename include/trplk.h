@@ -259,11 +259,13 @@ trplk_status trplk_rotate(trplk_handle* h, int dtype, int64_t n, int64_t ld, int
                           const void* U, const double* Y, int ldY, void* Xout);
 
 /* The same rotation on the tensor cores, FP32 U and Xout (trplk_rotate takes
- * this path for FP32 data when k >= 24): each 128-row tile of U is one
- * tcgen05.mma product with Y^T in tensor memory, BF16 operands from an exact
- * three-way split of every FP32 value (and of Y to FP32 accuracy), the six
- * products of parts whose order adds up to at most two summed in FP32, so the
- * result keeps FP32 accuracy.  w <= 64, k <= 32; EINVAL otherwise. */
+ * this path for FP32 data when w k >= 480; the solver for B = I): each
+ * 128-row tile of U is multiplied by Y on tcgen05.mma with FP32 accumulation
+ * in tensor memory, BF16 operands from an exact three-way split of every FP32
+ * value (and of Y to FP32 accuracy), the six products of parts whose order
+ * adds up to at most two summed in FP32, so the result keeps FP32 accuracy.
+ * ld a multiple of 128 (any ld the library allocates), U 16-byte aligned,
+ * w <= 64, k <= 32; EINVAL otherwise. */
 trplk_status trplk_rotate_tc(trplk_handle* h, int64_t n, int64_t ld, int w, int k, const float* U,
                              const double* Y, int ldY, float* Xout);
 

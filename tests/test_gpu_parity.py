@@ -438,10 +438,34 @@ def test_tensor_core_rotation_matches_definition(lib, h, w, k):
     print("tensor-core rotation w", w, "k", k, "error / (max|U| sqrt(w))", err)
     assert err <= 2e-6
     assert np.all(X.cpu().numpy()[:, n:] == 0)
-    # the dispatching entry agrees (it takes this path for k >= 24)
+    # the dispatching entry agrees (it takes this path for w k >= 480)
     X2 = torch.zeros((k, ld), dtype=torch.float32, device="cuda")
     lib.trplk_rotate(h, lib.F32, n, ld, w, k, Ud, Yd, w, X2)
     assert np.abs(X2.cpu().numpy()[:, :n].T - Xref).max() <= 2e-6 * np.abs(Uq).max() * math.sqrt(w)
+
+
+@pytest.mark.parametrize("w,k", [(16, 6), (40, 20), (50, 25), (64, 32)])
+def test_tensor_core_rotation_many_tiles_per_cta(lib, h, w, k):
+    """The rotation's pipeline over many tiles per CTA (n = 300,007: 2,344
+    tiles of 128 rows on one CTA per SM, so every staged-tile slot, operand set
+    and tensor-memory accumulator is reused many times, with its barrier
+    parities) against U Y in FP64, at the FP32 rotation's tolerance; the
+    padding rows stay zero."""
+    n = 300_007
+    rng = np.random.default_rng(w * 7 + k)
+    U = rng.standard_normal((n, w)) / math.sqrt(n)
+    Yc = np.linalg.qr(rng.standard_normal((w, w)))[0]
+    ld = ld_of(n)
+    Ud = padded(U, ld, torch.float32)
+    Yd = torch.from_numpy(Yc.ravel(order="F")).cuda()
+    X = torch.full((k, ld), float("nan"), dtype=torch.float32, device="cuda")
+    X[:, n:] = 0
+    lib.trplk_rotate_tc(h, n, ld, w, k, Ud, Yd, w, X)
+    Uq = U.astype(np.float32).astype(np.float64)
+    Xref = Uq @ Yc[:, :k]
+    got = X.cpu().numpy()[:, :n].T.astype(np.float64)
+    assert np.abs(got - Xref).max() <= 2e-6 * np.abs(Uq).max() * math.sqrt(w)
+    assert np.all(X.cpu().numpy()[:, n:] == 0)
 
 
 # ---------------------------------------------------------------- start block (bit-exact)

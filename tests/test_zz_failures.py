@@ -110,3 +110,31 @@ def test_wait_timeout_returns_etimeout_and_the_handle_recovers(lib, h):
     ev, X, res, rc, info = lib.solve(h, dev_csr(lib, A), None, p=2, q=12, k=4, l=1, tol=1e-8,
                                      precision=lib.PRECISION_MIXED)
     assert rc == lib.OK and np.all(res <= 1e-8)
+
+
+def test_tensor_core_rotation_timeout_returns_etimeout_and_recovers(lib, h):
+    """The tensor-core rotation's bounded waits made to run out (wait limit 0):
+    every warp role gives up at its first wait, the CTA agrees on it through
+    shared memory, waits for the tensor copies its producer already issued,
+    frees its tensor memory and reports TRPLK_ETIMEOUT -- no hang, no fault --
+    and the same call with the default limit then gives U Y."""
+    n, w, k = 300_000, 40, 20
+    ld = (n + 255) // 256 * 256
+    rng = np.random.default_rng(9)
+    U = rng.standard_normal((n, w)) / np.sqrt(n)
+    Yc = np.linalg.qr(rng.standard_normal((w, w)))[0]
+    Ud = torch.zeros((w, ld), dtype=torch.float32, device="cuda")
+    Ud[:, :n] = torch.from_numpy(np.ascontiguousarray(U.T)).float().cuda()
+    Yd = torch.from_numpy(Yc.ravel(order="F")).cuda()
+    X = torch.zeros((k, ld), dtype=torch.float32, device="cuda")
+    lib.trplk_set_wait_limit(h, 0)
+    try:
+        with pytest.raises(lib.TrplkError) as e:
+            lib.trplk_rotate_tc(h, n, ld, w, k, Ud, Yd, w, X)
+        assert e.value.code == lib.ETIMEOUT
+    finally:
+        lib.trplk_set_wait_limit(h, -1)
+    lib.trplk_rotate_tc(h, n, ld, w, k, Ud, Yd, w, X)
+    Uq = Ud[:, :n].double().cpu().numpy().T
+    ref = Uq @ Yc[:, :k]
+    assert np.abs(X.cpu().numpy()[:, :n].T - ref).max() <= 2e-6 * np.abs(Uq).max() * np.sqrt(w)
