@@ -26,7 +26,8 @@ each mixed and FP64, on 20 held-out 128^3 operators (seeds 2000-2019).
 p_hat = 15), q1pencil96 (trilinear Q1 stiffness/mass pencil on 96^3
 elements, 20 smallest, q = 50, p_hat = 25), aniso128 (one held-out
 anisotropic 128^3 operator with the learned FSAI, compared against Jacobi and
-classical FSAI in both precisions).  `--learned-ops 0` skips the learned block.
+classical FSAI in both precisions).  `--learned-ops 0` skips the learned block;
+`--learned-all` adds classical FSAI in FP64, IC(0) in both paths and Jacobi mixed to it.
 
 `--impl reference` times the CPU oracle (FP64 numpy/scipy) instead.
 Multi-GPU: one process per GPU (torchrun); the path does not shard, so each
@@ -90,6 +91,8 @@ def parse():
                     help="run this many mixed solves of the workload with the library's per-kernel profiler on, "
                          "print the per-family launches, time and algorithmic bytes as one JSON line and exit "
                          "(the command profiler captures run; nothing else is timed)")
+    ap.add_argument("--learned-all", action="store_true",
+                    help="the learned block also runs classical FSAI in FP64, IC(0) in both paths and Jacobi mixed")
     ap.add_argument("--learned-ops", type=int, default=len(HELD_OUT_SEEDS),
                     help="held-out anisotropic 128^3 operators of the learned block (0 skips it)")
     args = ap.parse_args()
@@ -363,9 +366,15 @@ LEARNED_VARIANTS = [("learned_mixed", "fsai_learned", 1), ("learned_fp64", "fsai
                     ("classical_mixed", "fsai", 1), ("classical_fp64", "fsai", 0),
                     ("ic0_mixed", "ic0", 1), ("ic0_fp64", "ic0", 0),
                     ("jacobi_mixed", "jacobi", 1), ("jacobi_fp64", "jacobi", 0)]
+# the default run keeps the learned factor in both precisions, its strongest
+# rival (classical FSAI, mixed) and the baseline (Jacobi, FP64): about seven
+# minutes for 20 operators; --learned-all adds the other four (Jacobi mixed
+# alone takes 26 s per operator: its FP32 phase stalls and the FP64
+# refinement does most of the work)
+LEARNED_DEFAULT = ("learned_mixed", "learned_fp64", "classical_mixed", "jacobi_fp64")
 
 
-def learned_block(lib, h, dev, stream, weights, train_info, nops):
+def learned_block(lib, h, dev, stream, weights, train_info, nops, every_variant=False):
     """Learned FSAI against Jacobi, classical FSAI and IC(0) (the paper's kind
     of preconditioner, Sec. 5.4), each in the mixed and the plain FP64 path, on `nops` held-out anisotropic 128^3 operators (seeds
     2000...): per variant the mean seconds per solve (CUDA events on the
@@ -399,16 +408,18 @@ def learned_block(lib, h, dev, stream, weights, train_info, nops):
             raise RuntimeError(f"learned block: {precond} mixed={mixed} did not converge: {info.as_dict()}")
         return e0.elapsed_time(e1) / 1e3, info.as_dict(), ev_d.cpu().numpy().copy()
 
-    rows = {name: [] for name, _, _ in LEARNED_VARIANTS}
+    variants = [v for v in LEARNED_VARIANTS if every_variant or v[0] in LEARNED_DEFAULT]
+    rows = {name: [] for name, _, _ in variants}
     for i, seed in enumerate(HELD_OUT_SEEDS[:nops]):
         A = W.anisotropic_diffusion(N, seed)
         t = (torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.col).to(dev), torch.from_numpy(A.val).to(dev))
         Ad = lib.make_csr(*t)
-        if i == 0:   # warm-up: module loading, first allocations
-            for _, pc, mx in LEARNED_VARIANTS:
-                solve(Ad, pc, mx)
+        if i == 0:   # warm-up: module loading, first allocations (one solve per preconditioner and path)
+            for _, pc, mx in variants:
+                if pc != "jacobi" or not mx:
+                    solve(Ad, pc, mx)
         res = {}
-        for name, pc, mx in LEARNED_VARIANTS:
+        for name, pc, mx in variants:
             res[name] = solve(Ad, pc, mx)
         base = res["jacobi_fp64"][2]
         for name, (sec, info, ev) in res.items():
@@ -432,7 +443,8 @@ def learned_block(lib, h, dev, stream, weights, train_info, nops):
     jf = summary["jacobi_fp64"]["mean_seconds"]
     out = {"family": "anisotropic 7-point diffusion 128^3 (axis factors loguniform[1, 100], coefficients "
                      "lognormal(0, 1.5)), p = 20, q = 50, p_hat = 25, +K = 1, tol 1e-8",
-           "held_out_seeds": HELD_OUT_SEEDS[:nops], "training": train_info, "summary": summary,
+           "held_out_seeds": HELD_OUT_SEEDS[:nops], "variants": [v[0] for v in variants], "training": train_info,
+           "summary": summary,
            "speedup_learned_mixed_vs_jacobi_fp64": jf / summary["learned_mixed"]["mean_seconds"],
            "speedup_learned_mixed_vs_learned_fp64": summary["learned_fp64"]["mean_seconds"]
            / summary["learned_mixed"]["mean_seconds"],
@@ -653,7 +665,7 @@ def run_ours(args, world, rank, local, pg):
 
     # the learned preconditioner on held-out operators of its family
     if args.learned_ops > 0:
-        out["learned"] = learned_block(lib, h, dev, stream, weights, train_info, args.learned_ops)
+        out["learned"] = learned_block(lib, h, dev, stream, weights, train_info, args.learned_ops, args.learned_all)
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
