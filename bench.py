@@ -18,8 +18,9 @@ host memory (`e2e`), the roofline of the dominant kernel family measured with
 CUDA events inside the timed region, the SpMV bandwidth, the CPU oracle on a
 bounded sample (`cpu_baseline`), and the learned preconditioner on the
 anisotropic 128^3 family (`learned`): an MLP trained on 200 seeded 32^3
-operators (seeds 1000-1199), then learned FSAI, Jacobi and classical FSAI,
-each mixed and FP64, on 20 held-out 128^3 operators (seeds 2000-2019).
+operators (seeds 1000-1199), then learned FSAI (mixed and FP64), classical
+FSAI (mixed) and Jacobi (FP64) on 20 held-out 128^3 operators (seeds
+2000-2019).
 
 `--workload` selects another operator class for the headline: diffusion128
 (3D 7-point lognormal(0, 1) diffusion on 128^3, 10 smallest, q = 40,
