@@ -186,6 +186,48 @@ template <> struct AccFast<float> {
   __device__ __forceinline__ void shfl_down_add(int off) { p += __shfl_down_sync(0xffffffffu, p, off); }
 };
 
+// Part<S>: one CTA's partial sum of a projection, as the grid reduction
+// moves it.  FP64 path: the double.  FP32 path: the compensated pair (p, s)
+// itself, packed into the 8 bytes of a double slot, and added pairwise by
+// TwoSum in FP32 -- the last CTA's sum over every CTA then runs on the FP32
+// pipe instead of the FP64 pipe (64 times slower on this GPU); its rounding
+// (about u^2 times the sum of |p|) stays far below the partials' own.
+template <typename S> struct Part;
+template <> struct Part<double> {
+  double v;
+  __device__ __forceinline__ void zero() { v = 0.0; }
+  __device__ __forceinline__ void add(const Part& o) { v += o.v; }
+  __device__ __forceinline__ double value() const { return v; }
+  __device__ __forceinline__ void store(double* slot) const { *slot = v; }
+  __device__ __forceinline__ void load(const double* slot) { v = *slot; }
+  __device__ __forceinline__ void shfl_down_add(int off) { v += __shfl_down_sync(0xffffffffu, v, off); }
+  __device__ __forceinline__ static Part of(const Acc<double>& a) { return Part{a.v}; }
+};
+template <> struct Part<float> {
+  float p, s;
+  __device__ __forceinline__ void zero() { p = 0.f; s = 0.f; }
+  __device__ __forceinline__ void add(const Part& o) {
+    float e;
+    two_sum(p, o.p, p, e);
+    s = __fadd_rn(s, __fadd_rn(e, o.s));
+  }
+  __device__ __forceinline__ double value() const { return (double)p + (double)s; }
+  __device__ __forceinline__ void store(double* slot) const { *reinterpret_cast<float2*>(slot) = make_float2(p, s); }
+  __device__ __forceinline__ void load(const double* slot) {
+    const float2 v = *reinterpret_cast<const float2*>(slot);
+    p = v.x;
+    s = v.y;
+  }
+  __device__ __forceinline__ void shfl_down_add(int off) {
+    Part o;
+    o.p = __shfl_down_sync(0xffffffffu, p, off);
+    o.s = __shfl_down_sync(0xffffffffu, s, off);
+    add(o);
+  }
+  __device__ __forceinline__ static Part of(const Acc<float>& a) { return Part{a.p, a.s}; }
+  __device__ __forceinline__ static Part of(const AccFast<float>& a) { return Part{a.p, 0.f}; }
+};
+
 // ----------------------------------------------------------------- device: mbarrier + bulk copy
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -494,18 +494,22 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
           if (TWO) acc1[j].shfl_down_add(off);
         }
         if (lane == 0) {
-          s_task[t] = acc0[j].value();
-          if (TWO) s_task[NQ * kMaxQ + t] = acc1[j].value();
+          Part<S>::of(acc0[j]).store(&s_task[t]);
+          if (TWO) Part<S>::of(acc1[j]).store(&s_task[NQ * kMaxQ + t]);
         }
       }
     }
     __syncthreads();
     for (int o = tid; o < (TWO ? 2 : 1) * w; o += blockDim.x) {
       const int r = o / w, c = o - r * w;
-      double t = 0.0;
+      Part<S> t, x;
+      t.load(&s_task[r * NQ * kMaxQ + c * NQ]);
 #pragma unroll
-      for (int h = 0; h < NQ; ++h) t += s_task[r * NQ * kMaxQ + c * NQ + h];
-      part[r * kMaxQ + c] = t;
+      for (int h = 1; h < NQ; ++h) {
+        x.load(&s_task[r * NQ * kMaxQ + c * NQ + h]);
+        t.add(x);
+      }
+      t.store(&part[r * kMaxQ + c]);
     }
   } else if (KIND == TS_UPDNORM || KIND == TS_DOT) {
 #pragma unroll
@@ -529,7 +533,9 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
   if (TASKS) {
     const int nout = TWO ? 2 * w : w;   // outputs o < w -> out0[o], else out1[o - w]
     for (int o0 = warp * 4; o0 < nout; o0 += nwarps * 4) {
-      double t[4] = {0.0, 0.0, 0.0, 0.0};
+      Part<S> t[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) t[u].zero();
       int col[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -539,29 +545,32 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
       // the loads of eight CTAs' partials are issued before they are added
       // (in the same order as one at a time: the sums are unchanged)
       for (int b0 = lane; b0 < nb; b0 += 32 * 8) {
-        double pv[8][4];
+        Part<S> pv[8][4];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int b = b0 + 32 * q;
           const double* pb = a.partials + (size_t)b * a.pstride;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) pv[q][u] = (b < nb && o0 + u < nout) ? pb[col[u]] : 0.0;
+          for (int u = 0; u < 4; ++u) {
+            if (b < nb && o0 + u < nout) pv[q][u].load(pb + col[u]);
+            else pv[q][u].zero();
+          }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            if (b0 + 32 * q < nb) t[u] += pv[q][u];
+            if (b0 + 32 * q < nb) t[u].add(pv[q][u]);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        for (int off = 16; off > 0; off >>= 1) t[u] += __shfl_down_sync(0xffffffffu, t[u], off);
+        for (int off = 16; off > 0; off >>= 1) t[u].shfl_down_add(off);
       if (lane == 0) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int o = o0 + u;
           if (o >= nout) continue;
-          double v = t[u];
+          double v = t[u].value();
           if (KIND == TS_RESID) v = sqrt(v);
           if (!isfinite(v)) atomicOr(a.status, kFlagNaN);
           if (o < w) a.out0[o] = v; else a.out1[o - w] = v;
