@@ -206,36 +206,43 @@ struct Operator {
   double norm1 = 0.0;
 };
 
+// Row pointers (thread per row) and column indices (thread per entry, so
+// every read is coalesced and no long row holds up a thread).
 __global__ void validate_csr_kernel(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
                                     int* status) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool bad = false;
+  for (int64_t i = t0; i < n; i += stride) {
     const int64_t a = rowptr[i], b = rowptr[i + 1];
-    if (a > b || a < 0 || b > nnz) {
-      atomicOr(status, 64);
-      continue;
-    }
-    for (int64_t e = a; e < b; ++e)
-      if (col[e] < 0 || col[e] >= n) atomicOr(status, 64);
+    bad |= a > b || a < 0 || b > nnz;
   }
+  for (int64_t e = t0; e < nnz; e += stride) bad |= col[e] < 0 || col[e] >= n;
+  if (bad) atomicOr(status, 64);
 }
 
 template <typename S>
 __global__ void row_abs_sum_kernel(int64_t n, const int64_t* rowptr, const S* val, double* out) {
-  // out[blockIdx.x] = max over the block's rows of sum_j |a_ij|
-  __shared__ double s_m[256];
+  // out[blockIdx.x] = max over the block's rows of sum_j |a_ij|; one warp per
+  // row, lanes striding it
+  __shared__ double s_m[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   double m = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
     double s = 0.0;
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) s += fabs((double)val[e]);
+    for (int64_t e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) s += fabs((double)val[e]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     m = s > m ? s : m;
   }
-  s_m[threadIdx.x] = m;
+  if (lane == 0) s_m[warp] = m;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) s_m[threadIdx.x] = fmax(s_m[threadIdx.x], s_m[threadIdx.x + o]);
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, s_m[w]);
+    out[blockIdx.x] = t;
   }
-  if (threadIdx.x == 0) out[blockIdx.x] = s_m[0];
 }
 
 __global__ void set_diag_block_kernel(double* T, int ldT, int k, const double* theta) {
@@ -277,7 +284,7 @@ Operator make_operator(trplk_handle* h, const trplk_csr* M, const std::string& t
   // structural validation on the device (column range, monotone rows)
   h->clear_status();
   ProfScope ps1(c, PK_OTHER, 0.0);
-  validate_csr_kernel<<<std::max(1, std::min<int>((int)((op.n + 255) / 256), c.sms * 8)), 256, 0, c.stream>>>(
+  validate_csr_kernel<<<std::max(1, std::min<int>((int)((op.nnz + 255) / 256), c.sms * 8)), 256, 0, c.stream>>>(
       op.n, op.nnz, op.d.rowptr, op.d.col, c.status);
   check_launch("validate_csr");
   const int nb = std::max(1, std::min<int>((int)((op.n + 255) / 256), 1024));

@@ -376,15 +376,43 @@ __global__ void start_block_kernel(int64_t n, int64_t ld, int k, uint64_t seed, 
   }
 }
 
+// The diagonal entry of row i (the last one if the row stores it twice; 0 if
+// none), read by the 32 lanes of a warp striding the row; every lane returns it.
+template <typename S>
+__device__ __forceinline__ S row_diag_warp(int64_t i, const int64_t* __restrict__ rowptr,
+                                           const int32_t* __restrict__ col, const S* __restrict__ val, int lane) {
+  const int64_t a = rowptr[i], b = rowptr[i + 1];
+  int64_t at = -1;
+  S d = 0;
+  for (int64_t e = a + lane; e < b; e += 32)
+    if (col[e] == i) {
+      at = e;
+      d = val[e];
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int64_t at2 = __shfl_xor_sync(0xffffffffu, at, o);
+    const S d2 = __shfl_xor_sync(0xffffffffu, d, o);
+    if (at2 > at) {
+      at = at2;
+      d = d2;
+    }
+  }
+  return d;
+}
+
 template <typename S>
 __global__ void jacobi_dinv_kernel(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                    const S* __restrict__ val, S* __restrict__ dinv, int* status) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    S d = 0;
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
-      if (col[e] == i) d = val[e];
-    if (!(d != 0)) atomicOr(status, kFlagNaN);
-    dinv[i] = d != 0 ? (S)1 / d : (S)0;
+  // one warp per row (coalesced reads; a power-law row does not hold up a thread)
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    const S d = row_diag_warp<S>(i, rowptr, col, val, lane);
+    if (lane == 0) {
+      if (!(d != 0)) atomicOr(status, kFlagNaN);
+      dinv[i] = d != 0 ? (S)1 / d : (S)0;
+    }
   }
 }
 
@@ -406,11 +434,11 @@ __global__ void sweep_update_kernel(int64_t ld, const S* __restrict__ x, const S
 // diag[i] = a_ii (0 where the row has no diagonal entry)
 __global__ void diag_of_kernel(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                const double* __restrict__ val, double* __restrict__ diag) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double d = 0.0;
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
-      if (col[e] == i) d = val[e];
-    diag[i] = d;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    const double d = row_diag_warp<double>(i, rowptr, col, val, lane);
+    if (lane == 0) diag[i] = d;
   }
 }
 
@@ -609,7 +637,7 @@ void start_block(const Ctx& c, int64_t n, int64_t ld, int k, uint64_t seed, doub
 template <typename S>
 void jacobi_dinv(const Ctx& c, const DevCsr<S>& A, S* dinv) {
   ProfScope ps(c, PK_OTHER, 0.0);
-  jacobi_dinv_kernel<S><<<grid_for(c, A.n), 256, 0, c.stream>>>(A.n, A.rowptr, A.col, A.val, dinv, c.status);
+  jacobi_dinv_kernel<S><<<grid_for(c, A.n * 32), 256, 0, c.stream>>>(A.n, A.rowptr, A.col, A.val, dinv, c.status);
   check_launch("jacobi_dinv");
 }
 
@@ -663,7 +691,7 @@ template void ic0_apply<float>(const Ctx&, int64_t, const DevCsr<float>&, const 
 
 void diag_of(const Ctx& c, int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, double* diag) {
   ProfScope ps(c, PK_OTHER, 0.0);
-  diag_of_kernel<<<grid_for(c, n), 256, 0, c.stream>>>(n, rowptr, col, val, diag);
+  diag_of_kernel<<<grid_for(c, n * 32), 256, 0, c.stream>>>(n, rowptr, col, val, diag);
   check_launch("diag_of");
 }
 
