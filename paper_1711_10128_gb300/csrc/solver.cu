@@ -287,6 +287,8 @@ Operator make_operator(trplk_handle* h, const trplk_csr* M, const std::string& t
   validate_csr_kernel<<<std::max(1, std::min<int>((int)((op.nnz + 255) / 256), c.sms * 8)), 256, 0, c.stream>>>(
       op.n, op.nnz, op.d.rowptr, op.d.col, c.status);
   check_launch("validate_csr");
+  // no kernel reads the rows before their pointers are known to be in range
+  if (h->read_status() & 64) throw Error(TRPLK_EINVAL, tag + ": row pointers or column indices out of range");
   const int nb = std::max(1, std::min<int>((int)((op.n + 255) / 256), 1024));
   auto* part = static_cast<double*>(h->get("norm1.part", 1024 * sizeof(double)));
   ProfScope ps2(c, PK_OTHER, 0.0);
@@ -294,8 +296,7 @@ Operator make_operator(trplk_handle* h, const trplk_csr* M, const std::string& t
   check_launch("row_abs_sum");
   double* hp = h->host(1024);
   TRPLK_CUDA_TRY(cudaMemcpyAsync(hp, part, nb * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-  int st = h->read_status();
-  if (st & 64) throw Error(TRPLK_EINVAL, tag + ": row pointers or column indices out of range");
+  h->sync();
   op.norm1 = 0.0;
   for (int i = 0; i < nb; ++i) op.norm1 = std::max(op.norm1, hp[i]);
   if (need_f32) {

@@ -648,6 +648,45 @@ def test_invalid_arguments_are_rejected(lib, h):
     assert rc == lib.OK
 
 
+def test_every_parameter_rule_is_enforced(lib, h):
+    """Each rule of the solver's parameter check returns EINVAL with its own
+    message and leaves the handle usable; so do row pointers that run
+    backwards or past nnz (found by the device-side structure check)."""
+    A = W.laplacian_2d(10)
+    Ad = dev_csr(lib, A)
+    cases = [
+        (dict(p=2, q=12, k=4, l=1, tol=0.0), "tol"),
+        (dict(p=2, q=12, k=4, l=-1), "l must be"),
+        (dict(p=2, q=70, k=4, l=1), "q must be <= 64"),
+        (dict(p=2, q=40, k=33, l=1), "k (thick-restart size)"),
+        (dict(p=2, q=12, k=4, l=1, max_cycles=0), "max_cycles"),
+        (dict(p=2, q=12, k=4, l=1, precond=99), "preconditioner"),
+        (dict(p=2, q=12, k=4, l=1, locking=7), "locking"),
+        (dict(p=2, q=12, k=4, l=1, block=5), "block"),
+        (dict(p=2, q=8, k=4, l=2, block=3), "block"),
+        (dict(p=2, q=12, k=4, l=1, block=2, locking=lib.LOCKING_HARD), "soft locking"),
+        (dict(p=2, q=12, k=4, l=1, precision=5), "precision"),
+        (dict(p=2, q=12, k=4, l=1, precond=lib.PRECOND_FSAI_LEARNED), "mlp_weights"),
+    ]
+    for kw, msg in cases:
+        with pytest.raises(lib.TrplkError) as e:
+            lib.solve(h, Ad, None, **kw)
+        assert e.value.code == lib.EINVAL, kw
+        assert msg in lib.trplk_last_error(h), (kw, lib.trplk_last_error(h))
+    for broken in ("backwards", "past_nnz"):
+        rp = A.rowptr.copy()
+        if broken == "backwards":
+            rp[7] = rp[8] + 1
+        else:
+            rp[50] = A.nnz + 5
+        bad = W.Csr(rp, A.col.copy(), A.val.copy())
+        with pytest.raises(lib.TrplkError) as e:
+            lib.solve(h, dev_csr(lib, bad), None, p=2, q=10, k=4, l=1)
+        assert e.value.code == lib.EINVAL, broken
+    ev, X, res, rc, info = lib.solve(h, Ad, None, p=2, q=12, k=4, l=1, tol=1e-8)
+    assert rc == lib.OK
+
+
 def test_host_inputs_and_outputs(lib, h):
     """The e2e form: host CSR and host outputs through trplk_solve."""
     A = W.laplacian_2d(30)
