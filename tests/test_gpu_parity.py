@@ -667,12 +667,30 @@ def test_every_parameter_rule_is_enforced(lib, h):
         (dict(p=2, q=12, k=4, l=1, block=2, locking=lib.LOCKING_HARD), "soft locking"),
         (dict(p=2, q=12, k=4, l=1, precision=5), "precision"),
         (dict(p=2, q=12, k=4, l=1, precond=lib.PRECOND_FSAI_LEARNED), "mlp_weights"),
+        (dict(p=0, q=12, k=4, l=1), "need 1 <= p <= k"),
+        (dict(p=5, q=12, k=4, l=1), "need 1 <= p <= k"),
+        (dict(p=2, q=6, k=4, l=2), "need q >= k + max(l,1) + 1"),
+        (dict(p=2, q=5, k=4, l=0), "need q >= k + max(l,1) + 1"),
     ]
     for kw, msg in cases:
         with pytest.raises(lib.TrplkError) as e:
             lib.solve(h, Ad, None, **kw)
         assert e.value.code == lib.EINVAL, kw
         assert msg in lib.trplk_last_error(h), (kw, lib.trplk_last_error(h))
+    # q larger than n (n = 25), a pencil whose B has another n, and a wanted
+    # end other than the smallest eigenvalues
+    small = dev_csr(lib, W.laplacian_2d(5))
+    other_n = dev_csr(lib, W.laplacian_2d(11))
+    for args, kw, msg in [((small, None), dict(p=2, q=30, k=4, l=1), "q must be <= n"),
+                          ((Ad, other_n), dict(p=2, q=12, k=4, l=1), "A and B differ")]:
+        with pytest.raises(lib.TrplkError) as e:
+            lib.solve(h, *args, **kw)
+        assert e.value.code == lib.EINVAL and msg in lib.trplk_last_error(h), msg
+    prm = lib.make_params(2, 12, 4, 1)
+    prm.which = lib.SMALLEST + 1
+    with pytest.raises(lib.TrplkError) as e:
+        lib.trplk_solve(h, Ad, None, prm, None, np.zeros(2), np.zeros((2, 100)), np.zeros(2), lib.trplk_info())
+    assert e.value.code == lib.EINVAL and "SMALLEST" in lib.trplk_last_error(h)
     for broken in ("backwards", "past_nnz"):
         rp = A.rowptr.copy()
         if broken == "backwards":
