@@ -218,7 +218,14 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool producer = (warp == NW);
   const int w = a.w;
-  const int ntask = NQ * w;
+  // Projection tasks: task (c, h) sums column c over row slice h of every
+  // tile.  Consumer warp `warp` takes slice hs = warp / WPS and the columns
+  // cls, cls + WPS, cls + 2 WPS, ... of it (its j-th task is column
+  // cls + WPS j), so every task of a warp reads the same rows of the staged
+  // vectors; a lane owns the four consecutive rows i0 .. i0 + 3 of the slice.
+  constexpr int WPS = NW / NQ;
+  const int hs = warp / WPS, cls = warp - hs * WPS;
+  const int i0 = hs * SLICE + 4 * lane;
 
   if (KIND == TS_UPDPROJ || KIND == TS_UPDNORM || KIND == TS_UPD)
     for (int c = tid; c < w; c += blockDim.x) s_h[c] = (S)a.hcoef[c];
@@ -301,76 +308,68 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
       S* s_v = const_cast<S*>(st) + (size_t)(a.nmat * w + a.nvec) * TR;     // per-stage scratch
 
       if (KIND == TS_PROJ || KIND == TS_INNER || KIND == TS_RESID) {
-        // Row mapping of the task phase: in slice h a lane owns the four
-        // consecutive rows h*SLICE + 4*lane .. +3, read with 128-bit shared loads.
-        // The staged vector (and, for TS_INNER, the preconditioned vector) for
-        // both slices is held in registers for the whole tile.
-        V4<S> zq[NQ], vq[NQ];
-#pragma unroll
-        for (int h = 0; h < NQ; ++h) zq[h] = ld4(vst + h * SLICE + 4 * lane);
+        // Row mapping of the task phase: the warp's tasks all lie in its row
+        // slice hs, where a lane owns the four consecutive rows i0 .. i0+3,
+        // read with 128-bit shared loads; the staged vector (and, for
+        // TS_INNER, the preconditioned vector) of those rows stays in
+        // registers for the whole tile.
+        const V4<S> zq = ld4(vst + i0);
+        V4<S> vq = zq;
         if (KIND == TS_INNER) {
-          // no barrier: each warp forms the preconditioned vector for the whole
-          // tile; the lanes whose rows fall in row block `warp` store it
-#pragma unroll
-          for (int h = 0; h < NQ; ++h) {
-            const int i = h * SLICE + 4 * lane;
-            if (a.pmode == PM_GIVEN) {
-              vq[h] = ld4(vst + TR + i);
-            } else {
-              // the source of the new vector: the just-multiplied column (z, bg)
-              // or, in block TRPL+K, the column of the same sequence b back
-              const V4<S> zs = a.vsrc ? ld4(vst + a.vsrc * TR + i) : zq[h];
-              const V4<S> bg = ld4(vst + a.bsrc * TR + i);
-              const S rho = (S)a.rho;
-              V4<S> v;
-              v.x = zs.x - rho * bg.x;
-              v.y = zs.y - rho * bg.y;
-              v.z = zs.z - rho * bg.z;
-              v.w = zs.w - rho * bg.w;
-              if (a.pmode == PM_JACOBI) {
-                const V4<S> dv = ld4(vst + 2 * TR + i);
-                v.x *= dv.x;
-                v.y *= dv.y;
-                v.z *= dv.z;
-                v.w *= dv.w;
-              }
-              if ((i >> 5) == warp) st4(a.vout + row0 + i, v);
-              vq[h] = v;
+          // no barrier: each warp forms the preconditioned vector for its
+          // slice; the lanes whose rows fall in row block `warp` store it
+          if (a.pmode == PM_GIVEN) {
+            vq = ld4(vst + TR + i0);
+          } else {
+            // the source of the new vector: the just-multiplied column (z, bg)
+            // or, in block TRPL+K, the column of the same sequence b back
+            const V4<S> zs = a.vsrc ? ld4(vst + a.vsrc * TR + i0) : zq;
+            const V4<S> bg = ld4(vst + a.bsrc * TR + i0);
+            const S rho = (S)a.rho;
+            V4<S> v;
+            v.x = zs.x - rho * bg.x;
+            v.y = zs.y - rho * bg.y;
+            v.z = zs.z - rho * bg.z;
+            v.w = zs.w - rho * bg.w;
+            if (a.pmode == PM_JACOBI) {
+              const V4<S> dv = ld4(vst + 2 * TR + i0);
+              v.x *= dv.x;
+              v.y *= dv.y;
+              v.z *= dv.z;
+              v.w *= dv.w;
             }
+            if ((i0 >> 5) == warp) st4(a.vout + row0 + i0, v);
+            vq = v;
           }
         }
         const bool alias = (a.matsel[1] == a.matsel[0]);
-        // Tasks go in pairs (j, j+1) so two independent accumulation chains per
-        // right-hand side interleave; the second of the last pair may be idle.
+        // Tasks go in pairs (columns c, c + WPS) so two independent
+        // accumulation chains per right-hand side interleave; the second of
+        // the last pair may be idle.
 #pragma unroll
         for (int j = 0; j < MAXT; j += 2) {
-          const int t = warp + NW * j;
-          if (t >= ntask) break;   // warp-uniform branch
-          const int t2 = t + NW;
-          const bool two = t2 < ntask;
-          const int c = t / NQ, h = t - c * NQ;
-          const int c2 = two ? t2 / NQ : c, h2 = two ? t2 - c2 * NQ : h;
-          const int off = c * TR + h * SLICE + 4 * lane;
-          const int off2 = c2 * TR + h2 * SLICE + 4 * lane;
-          const V4<S> z = (NQ == 1 || h == 0) ? zq[0] : zq[NQ - 1];
-          const V4<S> z2 = (NQ == 1 || h2 == 0) ? zq[0] : zq[NQ - 1];
+          const int c = cls + WPS * j;
+          if (c >= w) break;   // warp-uniform branch
+          const bool two = c + WPS < w;
+          const int off = c * TR + i0;
+          const int off2 = two ? off + WPS * TR : off;
           const V4<S> u = ld4(m0 + off);
           const V4<S> u2 = ld4(m0 + off2);
+          const V4<S>& z = zq;
           if (KIND == TS_PROJ) {
             acc0[j].fma4(u.x, z.x, u.y, z.y, u.z, z.z, u.w, z.w);
-            if (two) acc0[j + 1].fma4(u2.x, z2.x, u2.y, z2.y, u2.z, z2.z, u2.w, z2.w);
+            if (two) acc0[j + 1].fma4(u2.x, z.x, u2.y, z.y, u2.z, z.z, u2.w, z.w);
             continue;
           }
           if (KIND == TS_INNER) {
-            const V4<S> v = (NQ == 1 || h == 0) ? vq[0] : vq[NQ - 1];
-            const V4<S> v2 = (NQ == 1 || h2 == 0) ? vq[0] : vq[NQ - 1];
+            const V4<S>& v = vq;
             const V4<S> b = alias ? u : ld4(m1 + off);
             const V4<S> b2 = alias ? u2 : ld4(m1 + off2);
             acc0[j].fma4(u.x, z.x, u.y, z.y, u.z, z.z, u.w, z.w);
             acc1[j].fma4(b.x, v.x, b.y, v.y, b.z, v.z, b.w, v.w);
             if (two) {
-              acc0[j + 1].fma4(u2.x, z2.x, u2.y, z2.y, u2.z, z2.z, u2.w, z2.w);
-              acc1[j + 1].fma4(b2.x, v2.x, b2.y, v2.y, b2.z, v2.z, b2.w, v2.w);
+              acc0[j + 1].fma4(u2.x, z.x, u2.y, z.y, u2.z, z.z, u2.w, z.w);
+              acc1[j + 1].fma4(b2.x, v.x, b2.y, v.y, b2.z, v.z, b2.w, v.w);
             }
             continue;
           }
@@ -378,7 +377,7 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
               if (q == 1 && !two) break;
-              const int cc = q ? c2 : c, oo = q ? off2 : off;
+              const int cc = q ? c + WPS : c, oo = q ? off2 : off;
               const V4<S> uu = q ? u2 : u;
               const S th = s_y[cc];
               const V4<S> ax = ld4(m1 + oo), bx = ld4(m2 + oo);
@@ -390,8 +389,16 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
         }
       } else if (KIND == TS_UPDPROJ || KIND == TS_UPDNORM || KIND == TS_UPD) {
         // v' = v - U h, thread per row, two chains
+        // (even columns into d0, odd into d1; coefficients read four at a time)
         S d0 = 0, d1 = 0;
         int c = 0;
+        for (; c + 3 < w; c += 4) {
+          const V4<S> hc = ld4(s_h + c);
+          d0 = fmaS(m0[c * TR + tid], hc.x, d0);
+          d1 = fmaS(m0[(c + 1) * TR + tid], hc.y, d1);
+          d0 = fmaS(m0[(c + 2) * TR + tid], hc.z, d0);
+          d1 = fmaS(m0[(c + 3) * TR + tid], hc.w, d1);
+        }
         for (; c + 1 < w; c += 2) {
           d0 = fmaS(m0[c * TR + tid], s_h[c], d0);
           d1 = fmaS(m0[(c + 1) * TR + tid], s_h[c + 1], d1);
@@ -405,23 +412,16 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
           // the tile's barrier; it also tells every consumer whether another
           // consumer warp gave up its wait for this tile
           if (consumer_sync_or<TR>(false)) { fail = true; break; }
-          V4<S> vq[NQ];
-#pragma unroll
-          for (int h = 0; h < NQ; ++h) vq[h] = ld4(s_v + h * SLICE + 4 * lane);
+          const V4<S> v = ld4(s_v + i0);
 #pragma unroll
           for (int j = 0; j < MAXT; j += 2) {
-            const int t = warp + NW * j;
-            if (t >= ntask) break;
-            const int t2 = t + NW;
-            const bool two = t2 < ntask;
-            const int cc = t / NQ, h = t - cc * NQ;
-            const int cc2 = two ? t2 / NQ : cc, h2 = two ? t2 - cc2 * NQ : h;
-            const V4<S> b = ld4(m1 + cc * TR + h * SLICE + 4 * lane);
-            const V4<S> b2 = ld4(m1 + cc2 * TR + h2 * SLICE + 4 * lane);
-            const V4<S> v = (NQ == 1 || h == 0) ? vq[0] : vq[NQ - 1];
-            const V4<S> v2 = (NQ == 1 || h2 == 0) ? vq[0] : vq[NQ - 1];
+            const int cc = cls + WPS * j;
+            if (cc >= w) break;
+            const bool two = cc + WPS < w;
+            const V4<S> b = ld4(m1 + cc * TR + i0);
+            const V4<S> b2 = ld4(m1 + (two ? cc + WPS : cc) * TR + i0);
             acc0[j].fma4(b.x, v.x, b.y, v.y, b.z, v.z, b.w, v.w);
-            if (two) acc0[j + 1].fma4(b2.x, v2.x, b2.y, v2.y, b2.z, v2.z, b2.w, v2.w);
+            if (two) acc0[j + 1].fma4(b2.x, v.x, b2.y, v.y, b2.z, v.z, b2.w, v.w);
           }
         }
       } else if (KIND == TS_ROT) {
@@ -486,8 +486,9 @@ __global__ void __launch_bounds__(Tile<S>::TR + 32, MinBlocks<S>::value) ts_kern
     if (!producer) {
 #pragma unroll
       for (int j = 0; j < MAXT; ++j) {
-        const int t = warp + NW * j;
-        if (t >= ntask) break;
+        const int c = cls + WPS * j;
+        if (c >= w) break;
+        const int t = c * NQ + hs;   // slot of task (c, hs)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
           acc0[j].shfl_down_add(off);
