@@ -490,6 +490,52 @@ def test_block_first_cycle_spans_the_block_krylov_space():
         assert np.linalg.norm(U[:, :c] - K @ (K.T @ U[:, :c])) <= 1e-9 * np.sqrt(c), c
 
 
+def test_block_sequences_keep_their_own_shifts():
+    """With a preconditioner that is not a multiple of I the shift of each
+    sequence shapes its Krylov space.  On a block-diagonal operator whose two
+    targets lie in different blocks (start columns supported on one block
+    each, so X, the residuals and Jacobi's M all respect the blocks), the two
+    sequences of block TRPL+K (b = 2) never mix: the first cycle's basis must
+    lie in span[X, K(C_1, P M r_1), K(C_2, P M r_2)] with
+    C_i = P M (A - theta_i I) and P = I - X X^T, each Krylov space built
+    explicitly with its own sequence's shift (R15)."""
+    N = 5
+    A1 = W.diffusion_3d(N, W.lognormal_field(N, 1.0, 11)).to_scipy()
+    A2 = W.diffusion_3d(N, W.lognormal_field(N, 1.0, 12)).to_scipy()
+    A = sp.block_diag([A1, A2]).tocsr()
+    m = A1.shape[0]
+    n = 2 * m
+    p, q, k, b = 2, 14, 4, 2
+    R0 = W.start_block(n, k, 7)
+    X0 = np.zeros((n, k))
+    for c in range(k):   # columns alternate between the two blocks
+        h = c % 2
+        X0[h * m:(h + 1) * m, c] = R0[h * m:(h + 1) * m, c]
+    X, AX, _, theta, _, _ = O.initial_rayleigh_ritz(A, lambda v: v.copy(), X0)
+    side = [int(np.linalg.norm(X[m:, c]) > np.linalg.norm(X[:m, c])) for c in range(b)]
+    assert sorted(side) == [0, 1] and theta[0] != theta[1]   # the targets sit in different blocks
+    r = O.solve(A, None, p, q, k, 0, 1e-14, X0, "jacobi", max_cycles=1, record=True, block=b)
+    U = r["trace"][0]["U"]
+    dinv = 1.0 / A.diagonal()
+    P = lambda v: v - X @ (X.T @ v)
+    per = (q - k) // b
+    seqs = []
+    for i in range(b):   # orthonormal basis of K(C_i, P M r_i), grown one vector at a time
+        v = P(dinv * (AX[:, i] - theta[i] * X[:, i]))
+        Q = [v / np.linalg.norm(v)]
+        while len(Q) < per:
+            z = P(dinv * (A @ Q[-1] - theta[i] * Q[-1]))
+            for _ in range(2):
+                for u in Q:
+                    z = z - u * (u @ z)
+            Q.append(z / np.linalg.norm(z))
+        seqs.append(np.array(Q).T)
+    for c in range(k + 1, q + 1):
+        counts = [len([a for a in range(k, c) if (a - k) % b == i]) for i in range(b)]
+        K = np.linalg.qr(np.hstack([X] + [seqs[i][:, :counts[i]] for i in range(b)]))[0]
+        assert np.linalg.norm(U[:, :c] - K @ (K.T @ U[:, :c])) <= 1e-9 * np.sqrt(c), c
+
+
 def test_block_closed_form_degenerate_pairs_and_accounting():
     """Block TRPL+K (b = 2) on the 2D Laplacian, whose wanted set holds
     exactly degenerate pairs: closed-form eigenvalues, orthonormal vectors,
