@@ -171,3 +171,44 @@ def test_bf16_mode_b3_gradient_matches_finite_differences():
     assert L != L64 and abs(L - L64) <= 4 * 2.0 ** -8 * abs(L64)
     for name in g:
         assert np.all(np.abs(g[name] - g64[name]) <= 0.1 * np.abs(g64[name]).max() + 1e-300), name
+
+
+def test_loss_scales_each_vector_by_its_jacobi_energy():
+    """F5: the energy part of the loss is the mean over the vectors of
+    c_v E_v with c_v = 1 / (v^T D^-1 v) and E_v from the A-norm identity
+    (computed here by a dense solve)."""
+    A = W.diffusion_3d(4, W.lognormal_field(4, 1.0, 9)).to_scipy()
+    Ad = A.toarray()
+    G = F.classical_fsai(A)
+    rng = np.random.default_rng(11)
+    V = rng.standard_normal((A.shape[0], 3)) * np.array([1.0, 10.0, 0.1])
+    d = np.diag(Ad)
+    want = 0.0
+    for c in range(V.shape[1]):
+        v = V[:, c]
+        x = np.linalg.solve(Ad, v)
+        Mv = F.apply_M(G, v)
+        want += ((x - Mv) @ Ad @ (x - Mv) - v @ x) / (v @ (v / d))
+    want /= V.shape[1]
+    _, _, parts = F.loss_and_grad_G(G, A, V)
+    assert abs(parts["E"] - want) <= 1e-10 * abs(want)
+
+
+@pytest.mark.parametrize("quant", [None, "bf16"])
+def test_first_layer_gradient_uses_the_features_the_network_saw(quant):
+    """dL/dW1[:, f] = x_f dL/db1 for a feature f that has the same value x_f
+    in every row (the chain rule through z1 = W1 x + b1): on the
+    constant-coefficient operator every diagonal is 6, so feature 0 is log 6
+    in FP64 and its bfloat16 rounding in the BF16 mode (F6)."""
+    dims = (4, 4, 4)
+    A = W.diffusion_3d(4).to_scipy()
+    p = F.init_mlp(2, hidden=8)
+    rng = np.random.default_rng(12)
+    p["W3"] = 0.1 * rng.standard_normal(p["W3"].shape)
+    p["b1"] = 0.1 * rng.standard_normal(p["b1"].shape)
+    V = rng.standard_normal((A.shape[0], 2))
+    _, g, _ = F.loss_and_grad_mlp(p, A, dims, V, quant=quant)
+    x0 = np.log(6.0) if quant is None else F.bf16_round(np.log(6.0))
+    assert np.abs(g["b1"]).max() > 0
+    assert np.allclose(g["W1"][:, 0], x0 * g["b1"], rtol=1e-12, atol=1e-14 * np.abs(g["b1"]).max())
+    assert quant is None or abs(x0 - np.log(6.0)) > 1e-4   # the rounding is visible at this tolerance

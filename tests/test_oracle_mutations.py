@@ -62,6 +62,16 @@ MUTANTS = [
      "d = np.maximum(a - rho * b, 1e-3 * a)", "d = a - rho * b"),
     ("trplk", "unrestarted Lanczos: T not mirrored",
      "T[j, : j + 1] = T[: j + 1, j]", "T[j, : j] = 0.0"),
+    ("trplk", "norm of A: smallest instead of largest absolute row sum",
+     "abs(A).sum(axis=1)).max()", "abs(A).sum(axis=1)).min()"),
+    ("trplk", "recheck returns to the first pair, not the first failing one",
+     "t = int(failing[0])", "t = 0"),
+    ("trplk", "+K vectors orthogonalised against X only, not [X, G]",
+     "C = BU[:, :w].T @ W\n                W = W - U[:, :w] @ C", "C = BU[:, :k].T @ W\n                W = W - U[:, :k] @ C"),
+    ("trplk", "restart keeps p_hat - 1 vectors",
+     "Yk = Y[:, :k]", "Yk = Y[:, :k - 1]"),
+    ("trplk", "shifted Jacobi ignores B",
+     "b = np.ones_like(a) if B is None else B.diagonal()", "b = np.ones_like(a)"),
     ("dense", "Jacobi rotation with the wrong sign on one side",
      "A[:, j] = s * ai + c * aj", "A[:, j] = -s * ai + c * aj"),
     ("dense", "2x2 Schur step: tau of the wrong sign",
@@ -82,6 +92,10 @@ MUTANTS = [
      "F[i, 7] = (aii - off_sum) / aii", "F[i, 7] = (aii + off_sum) / aii"),
     ("fsai", "softplus derivative dropped",
      "dO[i, 3] += gG[e] * sigmoid(o[i, 3]) / sq[i]", "dO[i, 3] += gG[e] / sq[i]"),
+    ("fsai", "loss vectors not scaled by their Jacobi energy",
+     "cv = 1.0 / float(v @ (dinv * v))", "cv = 1.0"),
+    ("fsai", "BF16 first-layer gradient from the unrounded features",
+     'g["W1"] = dh1.T @ F_', 'g["W1"] = dh1.T @ F'),
     ("fsai", "bfloat16 rounding without ties to even",
      "(b + 0x7FFF + ((b >> 16) & 1))", "(b + 0x8000)"),
 ]

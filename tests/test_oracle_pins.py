@@ -42,6 +42,17 @@ def fem_eigs(N, count):
     return np.sort((mu[:, None, None] + mu[None, :, None] + mu[None, None, :]).ravel())[:count]
 
 
+def test_norm_is_the_largest_absolute_row_sum():
+    """R1: ||A||_1 is the largest absolute row sum (for symmetric A also the
+    largest column sum): 8 for the 5-point Laplacian, and a hand-made
+    matrix whose largest row sum needs the absolute values."""
+    assert O.norm1(W.laplacian_2d(6).to_scipy()) == 8.0
+    M = sp.csr_matrix(np.array([[2.0, -3.0, 0.0], [-3.0, 1.0, 0.5], [0.0, 0.5, -4.0]]))
+    assert O.norm1(M) == 5.0
+    r = O.solve(W.laplacian_2d(12).to_scipy(), None, 2, 10, 4, 1, 1e-8, W.start_block(144, 4, 1), "jacobi")
+    assert r["normA"] == 8.0
+
+
 # ---------------------------------------------------------------- dense pieces
 @pytest.mark.parametrize("n", [1, 2, 7, 31])
 def test_jacobi_eigh_tridiagonal_closed_form(n):
@@ -217,6 +228,32 @@ def test_invariants_T_equals_UtAU_and_b_orthonormal_basis():
     T1 = r["trace"][1]["T"]
     th0 = r["trace"][0]["theta"][:5]
     assert np.allclose(T1[:5, :5], np.diag(th0), atol=1e-12 * np.abs(th0).max())
+
+
+def test_target_advance_and_recheck_follow_the_recorded_residuals():
+    """R9 on a solve whose soft-locked pairs drift: in every cycle the target
+    advances by one exactly when its residual (recorded after the cycle's
+    Rayleigh-Ritz step) is below tol; when the last target converges while an
+    earlier pair has drifted above tol, the next cycle targets the first such
+    pair.  This run (2D Laplacian 14 x 14, p = 5, l = 2) has such a return."""
+    A = W.laplacian_2d(14).to_scipy()
+    p, q, k, l, tol = 5, 14, 6, 2, 1e-8
+    r = O.solve(A, None, p, q, k, l, tol, W.start_block(A.shape[0], k, 32), "jacobi")
+    assert r["status"] == O.OK
+    h = r["history"]
+    returns = 0
+    for a, b in zip(h[:-1], h[1:]):
+        t, res = a["t"], a["resid"]
+        if res[t] > tol:
+            assert b["t"] == t
+        elif t + 1 < p:
+            assert b["t"] == t + 1
+        else:   # the last target converged: back to the first pair above tol
+            assert np.any(res > tol)
+            assert b["t"] == int(np.flatnonzero(res > tol)[0])
+            returns += 1
+    assert returns >= 1
+    assert np.all(h[-1]["resid"] <= tol)
 
 
 def test_ritz_values_never_increase():
