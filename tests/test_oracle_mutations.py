@@ -72,6 +72,8 @@ MUTANTS = [
      "Yk = Y[:, :k]", "Yk = Y[:, :k - 1]"),
     ("trplk", "shifted Jacobi ignores B",
      "b = np.ones_like(a) if B is None else B.diagonal()", "b = np.ones_like(a)"),
+    ("trplk", "breakdown in the first inner step not reported",
+     "            status = BREAKDOWN\n            break\n        # +K", "            pass\n        # +K"),
     ("dense", "Jacobi rotation with the wrong sign on one side",
      "A[:, j] = s * ai + c * aj", "A[:, j] = -s * ai + c * aj"),
     ("dense", "2x2 Schur step: tau of the wrong sign",

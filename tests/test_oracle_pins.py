@@ -389,6 +389,20 @@ def test_breakdown_on_an_invariant_krylov_space_still_gives_exact_eigenpairs():
     assert np.linalg.norm(A @ x - x) <= 1e-10
 
 
+def test_breakdown_status_when_the_restart_vector_lies_in_the_start_space():
+    """R5: a preconditioner that maps every residual into span(X) makes the
+    cycle's first Lanczos vector vanish under CGS2; nothing new can enter the
+    basis, so the solve stops in its first cycle with status breakdown (the
+    start block is no eigenspace: its residuals are not small)."""
+    A = W.laplacian_2d(10).to_scipy()
+    n, p, k = A.shape[0], 2, 4
+    X0 = W.start_block(n, k, 5)
+    Qx = np.linalg.qr(X0)[0]
+    r = O.solve(A, None, p, 12, k, 1, 1e-10, X0, lambda v: Qx @ (Qx.T @ v), max_cycles=50)
+    assert r["status"] == O.BREAKDOWN and r["cycles"] == 1
+    assert r["mv_A"] == k and np.all(r["resid"] > 1e-3)
+
+
 # ---------------------------------------------------------------- hard locking (R13), M(rho_i) (R14)
 @pytest.mark.parametrize("precond", ["jacobi", "jacobi_shifted"])
 def test_hard_locking_closed_form_accounting_and_locked_orthogonality(precond):
