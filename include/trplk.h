@@ -281,7 +281,7 @@ trplk_status trplk_residual_norms(trplk_handle* h, int dtype, int64_t n, int64_t
 trplk_status trplk_start_block(trplk_handle* h, int64_t n, int64_t ld, int k, uint64_t seed,
                                double* X);
 
-/* Final FP64 check (spec residual form): for i < p,
+/* Final FP64 check (the residual form of the stopping test): for i < p,
  *   resid[i] = ||A x_i - theta_i B x_i||_2 / (normA ||x_i||_2)
  * with fresh FP64 matvecs.  X double n x p (ld); A, B F64 on device
  * (B == NULL: identity).  resid: double[p] (device). */
