@@ -27,8 +27,9 @@ FSAI (mixed) and Jacobi (FP64) on 20 held-out 128^3 operators (seeds
 p_hat = 15), q1pencil96 (trilinear Q1 stiffness/mass pencil on 96^3
 elements, 20 smallest, q = 50, p_hat = 25), aniso128 (one held-out
 anisotropic 128^3 operator with the learned FSAI, compared against Jacobi and
-classical FSAI in both precisions).  `--learned-ops 0` skips the learned block;
-`--learned-all` adds classical FSAI in FP64, IC(0) in both paths and Jacobi mixed to it.
+classical FSAI in both precisions).  `--learned-ops 0` skips the learned block
+(which, like the CPU baseline, runs at N = 1 only); `--learned-all` adds
+classical FSAI in FP64, IC(0) in both paths and Jacobi mixed to it.
 
 `--impl reference` times the CPU oracle (FP64 numpy/scipy) instead.
 Multi-GPU: one process per GPU (torchrun); the path does not shard, so each
@@ -486,7 +487,7 @@ def run_ours(args, world, rank, local, pg):
     setup = {}
     weights, grid = None, (0, 0, 0)
     train_info = None
-    if P["precond"] == "fsai_learned" or args.learned_ops > 0:
+    if P["precond"] == "fsai_learned" or (args.learned_ops > 0 and world == 1):
         weights, tsec, l0, l1, nops, tN = train_learned_fsai(lib, h, dev)
         train_info = {"train_seconds": tsec, "train_ops": nops, "train_grid": tN, "train_loss_first": l0,
                       "train_loss_last": l1, "adam_steps": 20 * nops,
@@ -664,8 +665,9 @@ def run_ours(args, world, rank, local, pg):
         out["e2e"] = {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
         out["eig_err_vs_oracle"]["e2e"] = eig_error(ev_h.numpy(), oracle_ref)
 
-    # the learned preconditioner on held-out operators of its family
-    if args.learned_ops > 0:
+    # the learned preconditioner on held-out operators of its family (N = 1 only: several
+    # minutes of solves that a replica run would only repeat on every rank)
+    if args.learned_ops > 0 and world == 1:
         out["learned"] = learned_block(lib, h, dev, stream, weights, train_info, args.learned_ops, args.learned_all)
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
