@@ -587,6 +587,50 @@ def test_block_sequences_keep_their_own_shifts():
         assert np.linalg.norm(U[:, :c] - K @ (K.T @ U[:, :c])) <= 1e-9 * np.sqrt(c), c
 
 
+def test_block_step_taken_as_one_block_gives_the_same_basis():
+    """R15 builds the block basis column by column; since the b new vectors of
+    a block come from the previous block's matvecs alone, the same basis is
+    reached block by block: B-orthogonalise all b vectors against the basis
+    at once (two passes), orthonormalise them within the block (CGS2 column
+    by column), then take their b matvecs together.  Gram-Schmidt with
+    positive normalisation is unique, so both orders give the same vectors
+    (here: the first cycle on the Q1 pencil, Jacobi, b = 3, to rounding)."""
+    N = 5
+    A, B = W.fem_q1_pencil(N, np.random.default_rng(9).uniform(1, 10, (N, N, N)))
+    As, Bs = A.to_scipy(), B.to_scipy()
+    n = A.n
+    p, q, k, b = 3, 18, 6, 3
+    X0 = W.start_block(n, k, 6)
+    r = O.solve(As, Bs, p, q, k, 0, 1e-14, X0, "jacobi", max_cycles=1, record=True, block=b)
+    U_ref = r["trace"][0]["U"]
+    applyB = lambda v: Bs @ v
+    X, AX, BX, theta, _, _ = O.initial_rayleigh_ritz(As, applyB, X0)
+    dinv = 1.0 / As.diagonal()
+    U, BU = X.copy(), BX.copy()
+    V = np.column_stack([dinv * (AX[:, i] - theta[i] * BX[:, i]) for i in range(b)])
+    while U.shape[1] < q:
+        V = V[:, : q - U.shape[1]]
+        for _ in range(2):                      # the block against the basis
+            V = V - U @ (BU.T @ V)
+        new, Bnew = [], []
+        for c in range(V.shape[1]):             # within the block
+            v = V[:, c]
+            for _ in range(2):
+                for u, Bu in zip(new, Bnew):
+                    v = v - u * (Bu @ v)
+            Bv = applyB(v)
+            beta = np.sqrt(v @ Bv)
+            new.append(v / beta)
+            Bnew.append(Bv / beta)
+        Unew, BUnew = np.column_stack(new), np.column_stack(Bnew)
+        Z = As @ Unew                            # the block's b matvecs together
+        V = np.column_stack([dinv * (Z[:, i] - theta[i] * BUnew[:, i]) for i in range(Unew.shape[1])])
+        U, BU = np.hstack([U, Unew]), np.hstack([BU, BUnew])
+    assert U.shape == U_ref.shape
+    assert np.abs(U - U_ref).max() <= 1e-12 * np.abs(U_ref).max()
+    assert np.abs(U.T @ (Bs @ U) - np.eye(q)).max() <= 1e-10
+
+
 def test_block_closed_form_degenerate_pairs_and_accounting():
     """Block TRPL+K (b = 2) on the 2D Laplacian, whose wanted set holds
     exactly degenerate pairs: closed-form eigenvalues, orthonormal vectors,
