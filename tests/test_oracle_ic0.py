@@ -5,6 +5,7 @@ the truncated Neumann series and, once the sweeps reach the depth of the
 dependency graph, to an exact triangular solve; the preconditioner is
 symmetric positive definite and, with exact solves, (L L^T)^-1."""
 import numpy as np
+import pytest
 import scipy.sparse as sp
 import scipy.sparse.linalg as sla
 
@@ -64,3 +65,10 @@ def test_preconditioner_is_spd_and_tends_to_the_inverse_of_the_factor_product():
     Mx = np.column_stack([I.apply_M(L, E[:, j], 3 * 5) for j in range(n)])   # depth 13 on the 5^3 grid
     LLt = (L @ L.T).toarray()
     assert np.allclose(Mx @ LLt, np.eye(n), atol=1e-10)
+
+
+def test_non_positive_pivot_is_a_breakdown():
+    """I1: a symmetric matrix that is not positive definite on its pattern has
+    a non-positive pivot, which is raised, not taken."""
+    with pytest.raises(ValueError):
+        I.ic0(sp.csr_matrix(np.array([[1.0, 2.0], [2.0, 1.0]])))

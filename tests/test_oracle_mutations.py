@@ -74,6 +74,12 @@ MUTANTS = [
      "b = np.ones_like(a) if B is None else B.diagonal()", "b = np.ones_like(a)"),
     ("trplk", "breakdown in the first inner step not reported",
      "            status = BREAKDOWN\n            break\n        # +K", "            pass\n        # +K"),
+    ("trplk", "rank-deficient start block accepted",
+     "        if beta <= EPS_BREAKDOWN * beta0:\n            raise ValueError(\"start block is numerically rank deficient\")\n", ""),
+    ("trplk", "B matvecs counted for B = I",
+     "    cnt[\"mv_B\"] += mvB if Bm is not None else 0\n    t = 0", "    cnt[\"mv_B\"] += mvB\n    t = 0"),
+    ("trplk", "unrestarted Lanczos: matvec count off by one",
+     "            return float(theta), j + 1", "            return float(theta), j + 2"),
     ("dense", "Jacobi rotation with the wrong sign on one side",
      "A[:, j] = s * ai + c * aj", "A[:, j] = -s * ai + c * aj"),
     ("dense", "2x2 Schur step: tau of the wrong sign",
@@ -82,6 +88,8 @@ MUTANTS = [
      "lij = s / row[j][j]", "lij = s / np.sqrt(row[j][j])"),
     ("ic0", "sweep adds the off-diagonal part",
      "x = (b - Ls @ x) / d", "x = (b + Ls @ x) / d"),
+    ("ic0", "non-positive pivot taken",
+     "                if not s > 0.0:\n                    raise ValueError(f\"IC(0) breakdown at row {i}: pivot {s}\")\n", ""),
     ("fsai", "classical FSAI row scaled by g_ii, not sqrt(g_ii)",
      "vals[rp[i]:rp[i + 1]] = gh / np.sqrt(gh[-1])", "vals[rp[i]:rp[i + 1]] = gh / gh[-1]"),
     ("fsai", "energy gradient with a wrong coefficient",

@@ -403,6 +403,23 @@ def test_breakdown_status_when_the_restart_vector_lies_in_the_start_space():
     assert r["mv_A"] == k and np.all(r["resid"] > 1e-3)
 
 
+def test_rank_deficient_start_block_is_rejected_and_counters_match_the_operator():
+    """R2: a start block with a dependent column cannot be B-orthonormalised
+    (error); with B = I no B matvec is counted, with a pencil the start block's
+    k B matvecs are."""
+    A = W.laplacian_2d(10).to_scipy()
+    X0 = W.start_block(100, 4, 5)
+    X0[:, 3] = 2.0 * X0[:, 1] - X0[:, 0]
+    with pytest.raises(ValueError):
+        O.solve(A, None, 2, 12, 4, 1, 1e-8, X0, "jacobi")
+    r = O.solve(A, None, 2, 12, 4, 1, 1e-8, W.start_block(100, 4, 5), "jacobi")
+    assert r["mv_B"] == 0
+    N = 4
+    Ap, Bp = W.fem_q1_pencil(N, np.ones((N, N, N)))
+    rp = O.solve(Ap.to_scipy(), Bp.to_scipy(), 2, 12, 4, 1, 1e-8, W.start_block(Ap.n, 4, 5), "jacobi", max_cycles=1)
+    assert rp["mv_B"] == 4 + (rp["mv_A"] - 4)   # the start block, then one B matvec per new vector
+
+
 # ---------------------------------------------------------------- hard locking (R13), M(rho_i) (R14)
 @pytest.mark.parametrize("precond", ["jacobi", "jacobi_shifted"])
 def test_hard_locking_closed_form_accounting_and_locked_orthogonality(precond):
@@ -502,6 +519,18 @@ def test_unrestarted_lanczos_closed_form_and_quasi_optimality():
     r = O.solve(As, None, 1, 18, 8, 1, 1e-9, x0, "none")
     assert r["status"] == O.OK
     assert mv <= r["mv_A"] <= 1.5 * mv
+
+
+def test_unrestarted_lanczos_stops_when_its_krylov_space_is_invariant():
+    """With two distinct eigenvalues the Krylov space of any start vector is
+    invariant after two steps: the residual identity gives zero there, so the
+    yardstick stops after exactly two matvecs with the smallest eigenvalue."""
+    rng = np.random.default_rng(13)
+    Q = np.linalg.qr(rng.standard_normal((30, 30)))[0]
+    lam = np.r_[np.full(10, 0.5), np.full(20, 3.0)]
+    A = sp.csr_matrix((Q * lam) @ Q.T)
+    th, mv = O.lanczos_unrestarted(A, rng.standard_normal(30), 1e-12)
+    assert mv == 2 and abs(th - 0.5) <= 1e-12
 
 
 def test_one_previous_vector_cuts_matvecs_for_five_pairs():
