@@ -212,3 +212,66 @@ def test_first_layer_gradient_uses_the_features_the_network_saw(quant):
     assert np.abs(g["b1"]).max() > 0
     assert np.allclose(g["W1"][:, 0], x0 * g["b1"], rtol=1e-12, atol=1e-14 * np.abs(g["b1"]).max())
     assert quant is None or abs(x0 - np.log(6.0)) > 1e-4   # the rounding is visible at this tolerance
+
+
+def test_kaporin_closed_form_and_the_loss_weight():
+    """K(D^-1/2) = log a for a constant diagonal a (G A G^T has unit diagonal);
+    the loss is E + 0.1 K with the same K as the stand-alone measure (F5)."""
+    A = W.diffusion_3d(4).to_scipy()                 # every diagonal entry is 6
+    G = sp.diags(1.0 / np.sqrt(A.diagonal())).tocsr()
+    assert abs(F.kaporin(G, A) - np.log(6.0)) <= 1e-14
+    B = W.diffusion_3d(4, W.lognormal_field(4, 1.0, 3)).to_scipy()
+    Gc = F.classical_fsai(B)
+    V = np.random.default_rng(4).standard_normal((B.shape[0], 2))
+    L, _, parts = F.loss_and_grad_G(Gc, B, V)
+    assert abs(parts["K"] - F.kaporin(Gc, B)) <= 1e-12 * abs(parts["K"])
+    assert abs(L - (parts["E"] + 0.1 * parts["K"])) <= 1e-14 * max(1.0, abs(L))
+
+
+def _mlp_case(seed):
+    dims = (4, 4, 4)
+    A = W.diffusion_3d(4, W.lognormal_field(4, 1.0, 8), axis=(1.0, 3.0, 9.0)).to_scipy()
+    p = F.init_mlp(seed, hidden=8)
+    rng = np.random.default_rng(seed + 10)
+    p["W3"] = 0.1 * rng.standard_normal(p["W3"].shape)
+    p["b1"] = 0.1 * rng.standard_normal(p["b1"].shape)
+    p["b2"] = 0.1 * rng.standard_normal(p["b2"].shape)
+    V = rng.standard_normal((A.shape[0], 2))
+    return A, dims, p, V
+
+
+def test_bf16_mode_sees_only_the_rounded_weights():
+    """F6: the rounded network uses W1, W2, W3 only through their bfloat16
+    roundings, forward and backward alike, so moving every weight inside its
+    rounding interval changes neither the loss nor any gradient."""
+    A, dims, p, V = _mlp_case(5)
+    L, g, _ = F.loss_and_grad_mlp(p, A, dims, V, quant="bf16")
+    q = dict(p)
+    for name in ("W1", "W2", "W3"):
+        w = p[name]
+        moved = w * (1.0 + 1e-5) + 1e-30        # far inside an interval of relative width 2^-8
+        keep = F.bf16_round(moved) == F.bf16_round(w)
+        q[name] = np.where(keep, moved, w)
+        assert keep.mean() > 0.9 and np.any(q[name] != w)
+    L2, g2, _ = F.loss_and_grad_mlp(q, A, dims, V, quant="bf16")
+    assert L2 == L
+    for name in g:
+        assert np.array_equal(g2[name], g[name]), name
+
+
+def test_bf16_forward_rounds_where_the_reading_says():
+    """F6 composed independently with torch's bfloat16 conversion: features
+    through FP32, W1..W3 and both hidden activations rounded, biases not,
+    products and sums in FP64."""
+    torch = pytest.importorskip("torch")
+    A, dims, p, _ = _mlp_case(6)
+    Fe = F.features_7pt(A, dims)
+    bf = lambda a: torch.from_numpy(np.asarray(a, np.float64).astype(np.float32)).to(torch.bfloat16).to(
+        torch.float64).numpy()
+    h1 = bf(np.maximum(bf(Fe) @ bf(p["W1"]).T + p["b1"], 0.0))
+    h2 = bf(np.maximum(h1 @ bf(p["W2"]).T + p["b2"], 0.0))
+    o = h2 @ bf(p["W3"]).T + p["b3"]
+    got, _ = F.mlp_forward(p, Fe, quant="bf16")
+    assert np.allclose(got, o, rtol=1e-13, atol=1e-15)
+    plain, _ = F.mlp_forward(p, Fe)
+    assert not np.allclose(plain, o, rtol=1e-6)      # the roundings are visible

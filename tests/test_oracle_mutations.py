@@ -106,6 +106,19 @@ MUTANTS = [
      "cv = 1.0 / float(v @ (dinv * v))", "cv = 1.0"),
     ("fsai", "BF16 first-layer gradient from the unrounded features",
      'g["W1"] = dh1.T @ F_', 'g["W1"] = dh1.T @ F'),
+    ("fsai", "BF16 mode: second hidden activation not rounded",
+     "    h2 = q(np.maximum(z2, 0.0))", "    h2 = np.maximum(z2, 0.0)"),
+    ("fsai", "BF16 mode: W2 not rounded in the forward pass",
+     'z2 = h1 @ q(p["W2"]).T + p["b2"]', 'z2 = h1 @ p["W2"].T + p["b2"]'),
+    ("fsai", "BF16 mode: backward through the unrounded W3",
+     'dh2 = dO @ q(p["W3"]) * (z2 > 0)', 'dh2 = dO @ p["W3"] * (z2 > 0)'),
+    ("fsai", "BF16 mode: backward through the unrounded W2",
+     'dh1 = dh2 @ q(p["W2"]) * (z1 > 0)', 'dh1 = dh2 @ p["W2"] * (z1 > 0)'),
+    ("fsai", "Kaporin weight 0.2 instead of 0.1",
+     "GAMMA = 0.1", "GAMMA = 0.2"),
+    ("fsai", "Kaporin measure with the sum instead of the mean",
+     "    return float(np.log(d.mean()) - 2.0 * np.mean(np.log(G.diagonal())))",
+     "    return float(np.log(d.sum()) - 2.0 * np.mean(np.log(G.diagonal())))"),
     ("fsai", "bfloat16 rounding without ties to even",
      "(b + 0x7FFF + ((b >> 16) & 1))", "(b + 0x8000)"),
 ]
