@@ -80,6 +80,8 @@ MUTANTS = [
      "    cnt[\"mv_B\"] += mvB if Bm is not None else 0\n    t = 0", "    cnt[\"mv_B\"] += mvB\n    t = 0"),
     ("trplk", "unrestarted Lanczos: matvec count off by one",
      "            return float(theta), j + 1", "            return float(theta), j + 2"),
+    ("trplk", "restart vectors' preconditioner applications not counted",
+     '        cnt["prec"] += len(pend)\n', '        cnt["prec"] += 0\n'),
     ("dense", "Jacobi rotation with the wrong sign on one side",
      "A[:, j] = s * ai + c * aj", "A[:, j] = -s * ai + c * aj"),
     ("dense", "2x2 Schur step: tau of the wrong sign",

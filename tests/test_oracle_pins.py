@@ -533,6 +533,20 @@ def test_unrestarted_lanczos_stops_when_its_krylov_space_is_invariant():
     assert mv == 2 and abs(th - 0.5) <= 1e-12
 
 
+def test_one_preconditioner_application_per_new_lanczos_vector():
+    """Accounting of Algorithm 1's M applications: each cycle applies M to
+    the restart residual and after each inner matvec but the last, i.e. once
+    per new Lanczos vector.  With l = 0 every matvec after the start block
+    belongs to an inner step, so the counts agree; +K vectors take matvecs
+    but no M."""
+    A = W.diffusion_3d(6, W.lognormal_field(6, 1.0, 4)).to_scipy()
+    X0 = W.start_block(A.shape[0], 6, 2)
+    r0 = O.solve(A, None, 3, 16, 6, 0, 1e-8, X0, "jacobi")
+    assert r0["status"] == O.OK and r0["prec"] == r0["mv_A"] - 6
+    r1 = O.solve(A, None, 3, 16, 6, 1, 1e-8, X0, "jacobi")
+    assert r1["status"] == O.OK and r1["mv_A"] - 6 - r1["cycles"] < r1["prec"] < r1["mv_A"] - 6
+
+
 def test_one_previous_vector_cuts_matvecs_for_five_pairs():
     """Fig. 3's trend without a preconditioner, p = 5: l = 1 needs clearly
     fewer matvecs than l = 0 (TRLan, Sec. 5.2) on the 2D Laplacian."""
