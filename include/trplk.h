@@ -28,7 +28,11 @@
  *  - Errors: every entry point returns a trplk_status; on anything but
  *    TRPLK_OK (and TRPLK_NOT_CONVERGED, whose outputs are still filled) the
  *    outputs are unspecified and trplk_last_error() says why.  Invalid
- *    arguments are detected on the host before any GPU work (TRPLK_EINVAL).
+ *    arguments are detected before the computation starts (TRPLK_EINVAL):
+ *    sizes and parameters on the host, the structure of a solver matrix
+ *    (row pointers in order and within nnz, column indices in [0, n)) by a
+ *    validation kernel whose result is read before any other kernel uses
+ *    the rows.
  */
 #ifndef TRPLK_H_
 #define TRPLK_H_
@@ -43,7 +47,7 @@ extern "C" {
 
 typedef enum {
   TRPLK_OK = 0,
-  TRPLK_EINVAL = 1,         /* bad argument (checked on the host)            */
+  TRPLK_EINVAL = 1,         /* bad argument or CSR structure                 */
   TRPLK_ENOMEM = 2,         /* device allocation failed                      */
   TRPLK_ECUDA = 3,          /* a CUDA call or kernel failed                  */
   TRPLK_NOT_CONVERGED = 4,  /* max_cycles reached; outputs hold the best pairs */
