@@ -82,6 +82,15 @@ MUTANTS = [
      "            return float(theta), j + 1", "            return float(theta), j + 2"),
     ("trplk", "restart vectors' preconditioner applications not counted",
      '        cnt["prec"] += len(pend)\n', '        cnt["prec"] += 0\n'),
+    ("trplk", "hard locking: X_prev not trimmed when pairs are locked",
+     "            Xprev_next = Xprev_next[:, min(s, Xprev_next.shape[1]):]", "            Xprev_next = Xprev_next[:, 0:]"),
+    ("trplk", "hard locking: at most one pair locked per cycle",
+     "        while s < pa and conv[s]:\n            s += 1", "        while s < min(pa, 1) and conv[s]:\n            s += 1"),
+    ("trplk", "hard locking: active outputs shifted by one vector",
+     "    evecs = np.hstack([Q, X[:, : max(0, p - nq)]])[:, :p]",
+     "    evecs = np.hstack([Q, X[:, 1: max(0, p - nq) + 1]])[:, :p]"),
+    ("trplk", "X_prev capped at p_hat instead of p",
+     "        Xprev_next = X[:, t: min(t + l, p)].copy()", "        Xprev_next = X[:, t: min(t + l, k)].copy()"),
     ("dense", "Jacobi rotation with the wrong sign on one side",
      "A[:, j] = s * ai + c * aj", "A[:, j] = -s * ai + c * aj"),
     ("dense", "2x2 Schur step: tau of the wrong sign",

@@ -448,6 +448,68 @@ def test_hard_locking_closed_form_accounting_and_locked_orthogonality(precond):
             assert np.abs(tr["QtBU"]).max() <= 1e-12
 
 
+def test_hard_locking_locks_each_leading_converged_run_and_trims_x_prev():
+    """R13 cycle by cycle against the recorded residuals: a cycle locks
+    exactly the leading run of its active pairs below tol (several at once
+    when they converge together), and the next cycle's X_prev holds the
+    min(l, active wanted) leading Ritz vectors less the ones just locked."""
+    p, q, k, l, tol = 6, 16, 8, 2, 1e-10
+    A = W.diffusion_3d(7, W.lognormal_field(7, 1.0, 5)).to_scipy()   # distinct eigenvalues
+    # three start columns within 1e-12 of eigenvectors: those pairs converge together
+    X0 = W.start_block(A.shape[0], k, 1).copy()
+    V = np.linalg.eigh(A.toarray())[1]
+    X0[:, :3] = V[:, :3] + 1e-12 * X0[:, :3]
+    r = O.solve(A, None, p, q, k, l, tol, X0, "jacobi", record=True, locking="hard")
+    assert r["status"] == O.OK
+    h, tr = r["history"], r["trace"]
+    multi = 0
+    for c in range(len(h) - 1):
+        res, nq = h[c]["resid"], h[c]["nq"]
+        run = 0
+        while run < res.size and res[run] <= tol:
+            run += 1
+        s = h[c + 1]["nq"] - nq
+        assert s == run, c
+        multi += s >= 2
+        assert tr[c + 1]["nprev"] == max(0, min(l, p - nq) - s), c
+    assert multi >= 1
+
+
+def test_returned_pairs_are_ritz_pairs_when_the_cycle_limit_stops_the_solve():
+    """Every returned value is the Rayleigh quotient of its returned vector
+    (B-normalised), also when max_cycles ends a solve with some pairs locked
+    and some still active (hard locking) or unconverged (soft locking)."""
+    N = 24
+    A = W.laplacian_2d(N).to_scipy()
+    for locking, cycles in (("hard", 30), ("soft", 4)):
+        r = O.solve(A, None, 6, 16, 8, 2, 1e-10, W.start_block(A.shape[0], 8, 1), "jacobi", max_cycles=cycles,
+                    locking=locking)
+        assert r["status"] == O.NOT_CONVERGED
+        if locking == "hard":
+            assert 0 < r["locked"] < 6
+        X = r["evecs"]
+        assert np.allclose(X.T @ X, np.eye(6), atol=1e-10)
+        assert np.abs(np.einsum("ij,ij->j", X, A @ X) - r["evals"]).max() <= 1e-10 * r["normA"]
+
+
+def test_x_prev_holds_the_targets_up_to_p():
+    """R7 with a +K block larger than the wanted pairs left: the next cycle's
+    X_prev is x_t .. x_min(t+l-1, p) of this cycle's start, less x_t when the
+    target converged (checked cycle by cycle against the recorded residuals)."""
+    A = W.laplacian_2d(20).to_scipy()
+    p, q, k, l, tol = 4, 16, 6, 3, 1e-10
+    r = O.solve(A, None, p, q, k, l, tol, W.start_block(A.shape[0], k, 3), "jacobi", record=True)
+    assert r["status"] == O.OK
+    h, tr = r["history"], r["trace"]
+    near_end = 0
+    for c in range(len(h) - 1):
+        t = h[c]["t"]
+        adv = 1 if h[c]["resid"][t] <= tol else 0
+        assert tr[c + 1]["nprev"] == min(t + l, p) - t - adv, c
+        near_end += t + l > p
+    assert near_end >= 1
+
+
 def test_hard_locking_generalized_pencil_brute_force():
     """Hard locking on the Q1 stiffness/mass pencil against a dense
     generalized eigensolve (B-inner products throughout, R3 + R13)."""
