@@ -72,3 +72,17 @@ def test_non_positive_pivot_is_a_breakdown():
     a non-positive pivot, which is raised, not taken."""
     with pytest.raises(ValueError):
         I.ic0(sp.csr_matrix(np.array([[1.0, 2.0], [2.0, 1.0]])))
+
+
+def test_preconditioner_applies_the_truncated_series_with_its_sweep_count():
+    """I3 as the solver sees it: preconditioner(A, s) applies P_s^T P_s with
+    P_s the explicit truncated Neumann series of s sweeps."""
+    A = W.diffusion_3d(5, W.lognormal_field(5, 1.0, 3)).to_scipy()
+    L = I.ic0(A)
+    d = L.diagonal()
+    Ls = (L - sp.diags(d)).toarray()
+    Dinv = np.diag(1.0 / d)
+    b = np.random.default_rng(1).standard_normal(A.shape[0])
+    for s in (1, 2, 3):
+        Ps = sum(np.linalg.matrix_power(-Dinv @ Ls, t) for t in range(s + 1)) @ Dinv
+        assert np.allclose(I.preconditioner(A, s)(b), Ps.T @ (Ps @ b), rtol=1e-12, atol=1e-14)

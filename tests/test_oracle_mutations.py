@@ -91,6 +91,8 @@ MUTANTS = [
      "    evecs = np.hstack([Q, X[:, 1: max(0, p - nq) + 1]])[:, :p]"),
     ("trplk", "X_prev capped at p_hat instead of p",
      "        Xprev_next = X[:, t: min(t + l, p)].copy()", "        Xprev_next = X[:, t: min(t + l, k)].copy()"),
+    ("trplk", "hard locking: inner step shifted by rho g, not rho B g",
+     "                v = Mapply(z - rho * BU[:, w - 1])", "                v = Mapply(z - rho * U[:, w - 1])"),
     ("dense", "Jacobi rotation with the wrong sign on one side",
      "A[:, j] = s * ai + c * aj", "A[:, j] = -s * ai + c * aj"),
     ("dense", "2x2 Schur step: tau of the wrong sign",
@@ -101,6 +103,8 @@ MUTANTS = [
      "x = (b - Ls @ x) / d", "x = (b + Ls @ x) / d"),
     ("ic0", "non-positive pivot taken",
      "                if not s > 0.0:\n                    raise ValueError(f\"IC(0) breakdown at row {i}: pivot {s}\")\n", ""),
+    ("ic0", "the solver's preconditioner takes one sweep more",
+     "    return lambda v: apply_M(L, v, sweeps)", "    return lambda v: apply_M(L, v, sweeps + 1)"),
     ("fsai", "classical FSAI row scaled by g_ii, not sqrt(g_ii)",
      "vals[rp[i]:rp[i + 1]] = gh / np.sqrt(gh[-1])", "vals[rp[i]:rp[i + 1]] = gh / gh[-1]"),
     ("fsai", "energy gradient with a wrong coefficient",

@@ -510,6 +510,27 @@ def test_x_prev_holds_the_targets_up_to_p():
     assert near_end >= 1
 
 
+def test_hard_locking_cycle_before_any_lock_is_the_soft_cycle():
+    """R13 on a pencil: until a pair is locked the active basis is the whole
+    basis, so each hard-locking cycle is an Algorithm 1 cycle with the
+    smallest pair as target -- the same Ritz values as the soft path, cycle
+    by cycle, as long as both target the first pair."""
+    N = 5
+    A, B = W.fem_q1_pencil(N, np.random.default_rng(7).uniform(1, 10, (N, N, N)))
+    As, Bs = A.to_scipy(), B.to_scipy()
+    p, q, k, l = 3, 16, 6, 1
+    X0 = W.start_block(A.n, k, 8)
+    rs = O.solve(As, Bs, p, q, k, l, 1e-10, X0, "jacobi", record=True)
+    rh = O.solve(As, Bs, p, q, k, l, 1e-10, X0, "jacobi", record=True, locking="hard")
+    same = 0
+    for hs, hh, ts, th in zip(rs["history"], rh["history"], rs["trace"], rh["trace"]):
+        if hs["t"] != 0 or hh["nq"] != 0:
+            break
+        assert np.allclose(th["theta"], ts["theta"], rtol=1e-12, atol=0)
+        same += 1
+    assert same >= 3
+
+
 def test_hard_locking_generalized_pencil_brute_force():
     """Hard locking on the Q1 stiffness/mass pencil against a dense
     generalized eigensolve (B-inner products throughout, R3 + R13)."""
